@@ -1,0 +1,117 @@
+/*
+ * mpv_oracle.h -- CPU oracle for the multi-scale fast MPV stereo matcher.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded restatement of
+ * what the matcher computes, written from the paper's definitions (Section 3.2,
+ * Section 3.3 and Section 3.4 of "A Robust Real-Time Computing-based Environment
+ * Sensing System for Intelligent Vehicle", arXiv 2001.09678).  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or constant with the CUDA library, and the CUDA library never
+ * loads it.
+ *
+ * All costs and energies are integers.  Energies are held in int64.
+ */
+#ifndef MPV_ORACLE_H
+#define MPV_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORA_INVALID 0xFFFFu
+#define ORA_NO_TRUNC 0x7FFFFFFF
+
+typedef struct {
+    int32_t max_disparity;  /* D: labels 0..D-1 at full resolution              */
+    int32_t num_scales;     /* S: pyramid levels, factor 2 (Section 3.4)          */
+    int32_t num_paths;      /* 4 (horizontal + vertical) or 8 (+ two diagonals)   */
+    int32_t p1;             /* lambda: penalty per pixel of disparity jump (Eq. EU) */
+    int32_t trunc;          /* T: truncation of the jump penalty, ORA_NO_TRUNC = none */
+    int32_t ssim_window;    /* N: SSIM patch side, 3 or 5                          */
+    int32_t window;         /* Dw at the finer levels; 0 selects D/4              */
+    int32_t block[4];       /* mode-block side per finer level (1 = interpolate)  */
+    int32_t lr_check;       /* 1: left-right consistency check on the output      */
+    int32_t lr_tol;         /* accepted |d_L - d_R| in pixels                      */
+} ora_params;
+
+/* Integer SSIM constants: round(C1 * n^2), round(C2 * n^2), n = N*N. */
+int64_t ora_c1(int N);
+int64_t ora_c2(int N);
+
+/* Matching cost of pixel (x,y) at absolute disparity u (Eq. components, Eq. ssim). */
+int32_t ora_ssim_cost(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch,
+                      int N, int x, int y, int u);
+
+/* Cost volume C[y][x][k], k in [0,Dw), disparity u = lo[y*W+x] + k (lo may be NULL = 0). */
+void ora_cost_volume(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, int N,
+                     const int32_t *lo, int Dw, int32_t *C);
+
+/* Min-convolution of the previous pixel's energies with the jump penalty
+ * (Eq. e(p,u)): M[k] = min_{v in [lo_prev, lo_prev+Dw)} A[v-lo_prev] + eps(lo+k, v),
+ * eps(u,v) = min(p1*|u-v|, T).  The naive form scans every pair (O(Dw^2)); the fast
+ * form is the two-sweep recursion of Section 3.3 (Eqs. 1-8).                        */
+void ora_envelope_naive(const int64_t *A, int lo_prev, int lo, int Dw, int64_t p1,
+                        int64_t T, int64_t *M);
+void ora_envelope_fast(const int64_t *A, int lo_prev, int lo, int Dw, int64_t p1,
+                       int64_t T, int64_t *M);
+
+/* One directional Viterbi pass (dx,dy) over the volume: L[y][x][k].
+ * normalized = 1: the bounded form L = C + M' - min_v L(prev, v);
+ * normalized = 0: the literal recursion E = C + M'.
+ * use_naive selects the O(Dw^2) envelope.  Returns 0, or -1 if the fast and naive
+ * envelopes ever disagree when check = 1.                                           */
+int ora_path(const int32_t *C, const int32_t *lo, int W, int H, int Dw, int dx, int dy,
+             int64_t p1, int64_t T, int normalized, int use_naive, int check, int64_t *L);
+
+/* Sum of the num_paths directional passes: S[y][x][k] (Eq. viterbi). */
+int ora_aggregate(const int32_t *C, const int32_t *lo, int W, int H, int Dw, int num_paths,
+                  int64_t p1, int64_t T, int normalized, int64_t *S);
+
+/* Winner-take-all: d = lo + argmin_k S, ties to the smallest k. */
+void ora_wta(const int64_t *S, const int32_t *lo, int W, int H, int Dw, uint16_t *d);
+
+/* 2x2 box down-sampling with round-half-up, odd edge replicated (Section 3.4). */
+void ora_downsample2(const uint8_t *in, int W, int H, int pitch, uint8_t *out, int out_pitch);
+
+/* Window lower bounds lo[y][x] of a finer level seeded from the coarser level's WTA
+ * map dprev (Wp x Hp): block mode (block >= 2) or linear interpolation (block == 1),
+ * then lo = clamp(c - Dw/2, 0, Dl - Dw).                                           */
+void ora_seed(const uint16_t *dprev, int Wp, int Hp, int W, int H, int block, int Dw,
+              int Dl, int32_t *lo);
+
+/* Level geometry of the pyramid; level 0 is the coarsest (Section 3.4 numbering). */
+void ora_level_dims(int W, int H, int S, int l, int *Wl, int *Hl);
+int ora_level_range(int D, int S, int l);   /* D_l = ceil(D / 2^(S-1-l))     */
+int ora_level_window(const ora_params *p, int l);  /* labels evaluated per pixel */
+
+/* Number of evaluated (pixel, label) nodes of one view (the work model, Eqs. Ot-O). */
+int64_t ora_node_count(int W, int H, const ora_params *p);
+
+/* Validates parameters against image size; 0 when usable. */
+int ora_check_params(int W, int H, const ora_params *p);
+
+/* One view of the matcher: pre-check WTA map of the finest level. */
+int ora_match_view(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch,
+                   const ora_params *p, uint16_t *d);
+
+/* Full matcher: left disparity with the left-right check (0xFFFF = rejected) and,
+ * when dR != NULL, the right view's map in right-image coordinates.               */
+int ora_match(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch,
+              const ora_params *p, uint16_t *dL, uint16_t *dR);
+
+/* Left-right check of two maps (right map in right-image coordinates). */
+void ora_lr_check(const uint16_t *dL, const uint16_t *dR, int W, int H, int tol,
+                  uint16_t *out);
+
+/* Per-level stage dump of one view: lo, cost and summed volume of level l.
+ * Buffers sized by ora_level_dims / ora_level_window.  Returns 0 on success.        */
+int ora_view_stage(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch,
+                   const ora_params *p, int level, int32_t *lo, int32_t *C, int64_t *S,
+                   uint16_t *d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
