@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 multi-scale MPV stereo matcher.
+
+Workload: one rectified 1280x720 uint8 pair per step, D = 128, 3 pyramid scales,
+8 scan paths, p1 = 10, T = 30, N = 5 SSIM windows, left-right check (both views).
+The pair is synthetic (slanted planes on Voronoi regions over gradient-noise texture),
+standing in for the paper's driving sequences.  Metric: Mdisp-evals/s = W*H*D / frame
+time (nominal full-range labels of one view), plus fps and p50/p99 latency.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+--impl reference times the CPU oracle (single-threaded C) on a bounded sample of the
+same workload: the reference arm of this method is the oracle.  Under torchrun every
+rank matches its own pair on its own GPU (replicas; no data-path collective).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, H, D = 1280, 720, 128
+PARAMS = dict(max_disparity=D, num_scales=3, num_paths=8, p1=10, trunc=30, ssim_window=5,
+              lr_check=1, lr_tol=1)
+METRIC = "Mdisp-evals/s at 1280x720 D=128 (3-scale MPV, 8 paths, left-right check)"
+UNIT = "Mdisp-evals/s"
+WORKLOAD = ("1280x720 uint8 pair, D=128, 3 scales (factor 2, windows D/4), 8 paths, "
+            "p1=10, T=30, N=5, left-right check")
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def nominal_units(w=W, h=H, d=D):
+    return w * h * d
+
+
+# ------------------------------------------------------------------------------------
+# Algorithmic bytes per stage (one frame, both views)
+# ------------------------------------------------------------------------------------
+
+def level_geometry():
+    levels = []
+    w, h = W, H
+    dims = []
+    for _ in range(PARAMS["num_scales"]):
+        dims.append((w, h))
+        w, h = (w + 1) // 2, (h + 1) // 2
+    dims = dims[::-1]
+    S = PARAMS["num_scales"]
+    for l, (w, h) in enumerate(dims):
+        sh = S - 1 - l
+        Dl = (D + (1 << sh) - 1) >> sh
+        Dw = Dl if l == 0 else min(D // 4, Dl)
+        levels.append((w, h, Dl, Dw))
+    return levels
+
+
+def algorithmic_bytes(views=2):
+    """Minimum HBM bytes per frame of each stage: the cost kernel writes the uint16
+    cost volume (2 B/node) after reading both images; the aggregation reads it (2 B/node)
+    and writes the uint16 summed volume (2 B/node); winner-take-all reads that (2 B/node)
+    and writes the uint16 map."""
+    cost = agg = wta = 0
+    nodes = 0
+    for (w, h, Dl, Dw) in level_geometry():
+        n = w * h * Dw
+        nodes += n
+        cost += views * (2 * n + 2 * w * h)
+        agg += views * (2 * n + 2 * n + 2 * w * h)
+        wta += views * (2 * n + 2 * w * h + 2 * w * h)
+    return dict(cost=cost, aggregate=agg, wta=wta), nodes
+
+
+# ------------------------------------------------------------------------------------
+# Clocks
+# ------------------------------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+
+    def summary(self):
+        self.f.seek(0)
+        rows = [ln.strip().split(",") for ln in self.f if ln.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                r = [x.strip() for x in r]
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------
+# Our arm
+# ------------------------------------------------------------------------------------
+
+def run_mine(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2001_09678_gb300 import mpv, synth
+
+    L, R, _ = synth.slanted_pair(W, H, seed=rank)
+    left = torch.from_numpy(L).to(dev)
+    right = torch.from_numpy(R).to(dev)
+    disp = torch.empty((H, W), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = mpv.mpv_create(local)
+    mpv.mpv_set_params(ctx, mpv.mpv_default_params(**PARAMS))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        mpv.mpv_match(ctx, left, right, disp, stream)
+    mpv.mpv_sync(ctx)
+    mpv.mpv_profile_read(ctx)  # reset counters
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mpv.mpv_profile_enable(ctx, True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)          # L2 flush between timed steps (not timed)
+            starts[i].record(stream)
+            mpv.mpv_match(ctx, left, right, disp, stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        wall = time.perf_counter() - t0
+    prof = mpv.mpv_profile_read(ctx)
+    mpv.mpv_profile_enable(ctx, False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps * nominal_units() / (total_ms / 1e3) / 1e6
+
+    # end to end through the host entry point: pinned host buffers, copies inside
+    hl = torch.from_numpy(L).pin_memory()
+    hr = torch.from_numpy(R).pin_memory()
+    hd = torch.empty((H, W), dtype=torch.int16).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        mpv.mpv_match_host(ctx, hl, hr, hd, stream)
+    barrier()
+    e2e_times = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        mpv.mpv_match_host(ctx, hl, hr, hd, stream)   # synchronizes before returning
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.steps * nominal_units() / e2e_s / 1e6
+    ok = np.array_equal(hd.numpy(), disp.cpu().numpy())
+
+    # roofline of the dominant kernel (by device time over the timed region)
+    alg, nodes = algorithmic_bytes()
+    stage_ms = {k: v[0] for k, v in prof.items()}
+    launches = sum(v[1] for v in prof.values())
+    dom = max(("cost", "aggregate", "wta"), key=lambda k: stage_ms[k])
+    peak, peak_kind = measured_peaks()
+    dom_s = stage_ms[dom] / 1e3
+    achieved = alg[dom] * args.steps / dom_s / 1e9 if dom_s > 0 else 0.0
+    kern_launches = prof[dom][1]
+
+    out = None
+    if rank == 0:
+        clk = clocks.summary()
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": W, "height": H, "max_disparity": D,
+                       "scales": 3, "paths": 8, "global_batch": world,
+                       "parallelism": f"replicas{world}",
+                       "l2": "flushed between timed steps (256 MiB device write, untimed)"},
+            "fps": round(1e3 / ms_per_step, 1),
+            "latency_ms": {"p50": round(statistics.median(step_ms), 4),
+                           "p99": round(sorted(step_ms)[min(len(step_ms) - 1,
+                                                            int(0.99 * len(step_ms)))], 4)},
+            "evaluated_nodes_per_view": nodes,
+            "stage_ms_per_step": {k: round(v / args.steps, 4) for k, v in stage_ms.items()},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "peak_source": peak_kind,
+                         "alg_bytes_per_step": alg[dom], "launches_per_step":
+                             kern_launches / args.steps,
+                         "traffic": None},
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
+                    "ms_per_step": round(1e3 * e2e_s / args.steps, 4),
+                    "matches_device_path": bool(ok)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "wall_s_timed_region": round(wall, 4),
+        }
+    mpv.mpv_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_full(L, R)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------------
+# The oracle on the host
+# ------------------------------------------------------------------------------------
+
+def _ora_params():
+    from oracle import ref
+    return ref.params(window=0, block=(0, 0, 0, 0), **PARAMS)
+
+
+def cpu_baseline_full(L, R):
+    """The oracle, single-threaded, on one full pair of the workload (both views)."""
+    from oracle import ref
+    p = _ora_params()
+    ref.lib()
+    t = time.perf_counter()
+    ref.match(L, R, p)
+    dt = time.perf_counter() - t
+    return {"value": round(nominal_units() / dt / 1e6, 3), "unit": UNIT, "cores": 1,
+            "kind": "oracle", "sample": "one full 1280x720 pair, 3 scales, both views",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import ref
+    from paper_2001_09678_gb300 import synth
+    L, R, _ = synth.slanted_pair(W, H, seed=0)
+    rows = 90                      # bounded sample: a 1280x90 strip through the matcher
+    y0 = (H - rows) // 2
+    Ls, Rs = L[y0:y0 + rows].copy(), R[y0:y0 + rows].copy()
+    p = _ora_params()
+    ref.lib()
+    for _ in range(args.warmup):
+        ref.match(Ls, Rs, p)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        ref.match(Ls, Rs, p)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    units = W * rows * D
+    value = args.steps * units / tot / 1e6
+    sample = f"1280x{rows} strip (rows {y0}..{y0 + rows - 1}) of the 1280x720 pair per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * tot / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": W, "height": H, "max_disparity": D,
+                   "scales": 3, "paths": 8},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("mine", "reference"), default="mine")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

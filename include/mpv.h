@@ -1,0 +1,180 @@
+/*
+ * mpv.h -- C ABI of the GB300 multi-scale fast MPV (Multi-Path-Viterbi) stereo matcher.
+ *
+ * The method is the stereo matcher of Section 3.2-3.4 of "A Robust Real-Time
+ * Computing-based Environment Sensing System for Intelligent Vehicle" (Xie, Long,
+ * Zhang, Sun; arXiv 2001.09678):
+ *   - an SSIM matching cost between N x N patches of the rectified left image I0 and
+ *     right image I1 (Section 3.2, Eq. components and Eq. ssim), kept as integers;
+ *   - bi-directional Viterbi passes along 4 or 8 scan directions with full
+ *     connectivity between disparity nodes under an L1 (total-variation) jump penalty
+ *     (Eq. EU, Eq. e(p,u)), evaluated by the O(2m) two-sweep recursion of Section 3.3;
+ *   - the sum of the path energies and winner-take-all (Eq. viterbi);
+ *   - the coarse-to-fine pyramid of Section 3.4: full range only at the top level,
+ *     finer levels search a per-pixel window seeded by block mode and, at the finest
+ *     level, interpolation (Eqs. Ot-O);
+ *   - a left-right consistency check on the output.
+ * Every cost and energy is an integer; results are bit-identical to the definition.
+ *
+ * Conventions shared by every entry point:
+ *   - Image and disparity pointers passed to mpv_match / mpv_match_batch are DEVICE
+ *     pointers owned by the caller; the library never frees them.  Images are uint8,
+ *     row-major, rows `pitch` bytes apart.  Disparities are uint16, rows `disp_pitch`
+ *     elements apart; MPV_INVALID marks a pixel rejected by the left-right check.
+ *   - A context owns its device workspace (grown on demand with cudaMalloc) and is
+ *     used by one host thread at a time.  There is no global state.
+ *   - Calls are asynchronous on `cuda_stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Device-side failures are latched in the context and returned by the
+ *     next call or by mpv_sync.
+ *   - Invalid arguments return MPV_ERR_INVALID_ARG and leave every output untouched.
+ *     No entry point aborts, traps or throws.
+ */
+#ifndef MPV_H
+#define MPV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpv_ctx mpv_ctx;
+
+typedef enum {
+    MPV_OK = 0,
+    MPV_ERR_INVALID_ARG = 1,  /* a parameter or size outside the documented range      */
+    MPV_ERR_UNSUPPORTED = 2,  /* valid request the library does not implement          */
+    MPV_ERR_OOM = 3,          /* workspace allocation failed or exceeds the byte budget */
+    MPV_ERR_CUDA = 4,         /* a CUDA runtime call failed                              */
+    MPV_ERR_TIMEOUT = 5,      /* a bounded device-side wait expired                      */
+    MPV_ERR_INTERNAL = 6      /* a device-side consistency check failed                  */
+} mpv_status;
+
+#define MPV_INVALID 0xFFFFu
+#define MPV_NO_TRUNC 0x7FFFFFFF
+
+#define MPV_MERGE_SUM 0         /* S = sum of the directional energies (Eq. viterbi)     */
+#define MPV_PROPOSAL_PYRAMID 0  /* finer-level windows from the coarser level (Sec. 3.4) */
+#define MPV_PROPOSAL_LEARNED 1  /* finest-level windows from the learned proposal        */
+
+/* Matcher parameters.  Fill with mpv_default_params, then override. */
+typedef struct {
+    uint32_t struct_size;   /* = sizeof(mpv_params); guards ABI evolution                  */
+    int32_t max_disparity;  /* D >= 1: labels 0..D-1 at full resolution (Eq. Ot's d)       */
+    int32_t num_scales;     /* S in [1,4]: pyramid levels, factor 2 (Section 3.4: S = 3)  */
+    int32_t num_paths;      /* 4 (left/right, up/down) or 8 (+ both diagonals; Table alg) */
+    int32_t p1;             /* lambda >= 0: penalty per pixel of disparity jump (Eq. EU)  */
+    int32_t trunc;          /* T >= 0: the jump penalty is min(p1*|du|, T); MPV_NO_TRUNC   */
+                            /* keeps the paper's untruncated form                          */
+    int32_t ssim_window;    /* N in {3,5}: SSIM patch side (Section 3.2, "N x N")          */
+    int32_t window;         /* Dw > 0: labels searched per pixel below the top level;      */
+                            /* 0 selects D/4 (Eqs. Ot1, Ot2)                               */
+    int32_t block[4];       /* mode-block side (in coarse pixels) for levels 1..S-1;       */
+                            /* 1 = per-pixel interpolation, 0 = default (2, 1 at finest)  */
+    int32_t lr_check;       /* 1: left-right check on the output, 0: raw left WTA map     */
+    int32_t lr_tol;         /* accepted |d_L - d_R| in pixels (default 1)                  */
+    int32_t merge_mode;     /* MPV_MERGE_SUM                                                */
+    int32_t proposal;       /* MPV_PROPOSAL_PYRAMID or MPV_PROPOSAL_LEARNED                */
+} mpv_params;
+
+/* One stereo pair of a batch.  All pointers are device pointers. */
+typedef struct {
+    const uint8_t *left;    /* I0, width x height, rows `pitch` bytes apart            */
+    const uint8_t *right;   /* I1, same geometry                                       */
+    int32_t width, height;
+    int32_t pitch;          /* bytes, >= width                                         */
+    int32_t max_disparity;  /* 0 = the context's D                                     */
+    uint16_t *disp;         /* output, rows disp_pitch elements apart                 */
+    int32_t disp_pitch;     /* elements, >= width                                      */
+    uint16_t *disp_right;   /* optional right-view map (right-image coordinates), NULL */
+} mpv_pair;
+
+/* Default parameters: D = 128, S = 3, 8 paths, p1 = 10, T = 30, N = 5, Dw = D/4,
+ * blocks {2,1}, left-right check on with tolerance 1, summed merge, pyramid windows. */
+mpv_status mpv_default_params(mpv_params *p);
+
+/* Creates a context on CUDA device `device`.  *out receives the handle. */
+mpv_status mpv_create(int device, mpv_ctx **out);
+
+/* Copies and validates `p` (MPV_ERR_INVALID_ARG: out of range; the context keeps its
+ * previous parameters).  Size-dependent checks are made by each match call.          */
+mpv_status mpv_set_params(mpv_ctx *ctx, const mpv_params *p);
+mpv_status mpv_get_params(const mpv_ctx *ctx, mpv_params *p);
+
+/* Disparity map of one rectified pair (left view), device pointers, asynchronous.
+ * Requirements: width, height >= N; 1 <= D <= min(width, 1024); the top pyramid level
+ * at least N x N; pitch >= width; disp_pitch >= width; and the bound on summed
+ * energies num_paths * (255 + min(T, p1 * (D - 1))) < 65535.                          */
+mpv_status mpv_match(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                     int32_t width, int32_t height, int32_t pitch, uint16_t *disp,
+                     int32_t disp_pitch, void *cuda_stream);
+
+/* Same as mpv_match on HOST buffers: the call copies the pair to the device, matches,
+ * copies the map back and synchronizes `cuda_stream` before returning.  Host buffers
+ * may be pageable or pinned (pinned overlaps better).                                 */
+mpv_status mpv_match_host(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                          int32_t width, int32_t height, int32_t pitch, uint16_t *disp,
+                          int32_t disp_pitch, void *cuda_stream);
+
+/* Matches n pairs of possibly different sizes and ranges in one submission.  Each pair
+ * is validated first; if any is invalid nothing is launched.  The batch is replayed
+ * from a CUDA graph when the same batch signature (sizes, ranges, pointers) repeats. */
+mpv_status mpv_match_batch(mpv_ctx *ctx, const mpv_pair *pairs, int32_t n, void *cuda_stream);
+
+/* Loads the learned-proposal network weights (used when proposal = LEARNED). */
+mpv_status mpv_load_proposal_weights(mpv_ctx *ctx, const char *path);
+
+/* Waits for the context's last submitted work and returns any latched device error. */
+mpv_status mpv_sync(mpv_ctx *ctx);
+
+/* Device bytes the context needs for a width x height pair at its parameters. */
+mpv_status mpv_workspace_bytes(const mpv_ctx *ctx, int32_t width, int32_t height,
+                               size_t *bytes);
+
+/* Caps the workspace (bytes; 0 = no cap).  A match that needs more returns MPV_ERR_OOM. */
+mpv_status mpv_set_workspace_limit(mpv_ctx *ctx, size_t bytes);
+
+/* Stage outputs of one pyramid level of one view, for verification.  view 0 is the
+ * left view, view 1 the right view (the matcher run on the mirrored, swapped pair).
+ * Device outputs, each may be NULL: lo (uint16 W_l x H_l, window starts), cost
+ * (uint16 W_l x H_l x Dw_l, u fastest), sum (uint32, same shape), disp (uint16 W_l x
+ * H_l pre-check WTA map).  Synchronous.                                                */
+mpv_status mpv_debug_stage(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                           int32_t width, int32_t height, int32_t pitch, int32_t view,
+                           int32_t level, uint16_t *lo, uint16_t *cost, uint32_t *sum,
+                           uint16_t *disp, void *cuda_stream);
+
+/* Level geometry used by the matcher: width, height, full range D_l and window Dw_l of
+ * level `level` (0 = coarsest) for a width x height pair.                            */
+mpv_status mpv_level_info(const mpv_ctx *ctx, int32_t width, int32_t height, int32_t level,
+                          int32_t *w, int32_t *h, int32_t *range, int32_t *window);
+
+/* Stages reported by the profiler. */
+#define MPV_STAGE_PYRAMID 0     /* mirroring and 2x2 down-sampling                      */
+#define MPV_STAGE_SEED 1        /* per-pixel windows of the finer levels                 */
+#define MPV_STAGE_COST 2        /* SSIM cost volume                                      */
+#define MPV_STAGE_AGGREGATE 3   /* directional Viterbi passes and their sum              */
+#define MPV_STAGE_WTA 4         /* winner-take-all                                       */
+#define MPV_STAGE_LR 5          /* left-right check                                      */
+#define MPV_NUM_STAGES 6
+
+/* on = 1: record a CUDA event pair around every kernel launch of later calls on the
+ * launch's own stream; on = 0: stop recording and drop what was recorded.          */
+mpv_status mpv_profile_enable(mpv_ctx *ctx, int32_t on);
+
+/* Synchronizes the recorded work, then writes for each stage k < n the summed device
+ * time ms[k] of its recorded launches and launches[k], the number of kernels the
+ * library launched for it since the previous read (counted with profiling on or off),
+ * and resets both.  Either array may be NULL.                                        */
+mpv_status mpv_profile_read(mpv_ctx *ctx, double *ms, int64_t *launches, int32_t n);
+
+const char *mpv_status_string(mpv_status s);
+
+/* Releases the context and its workspace; NULL is accepted. */
+void mpv_destroy(mpv_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

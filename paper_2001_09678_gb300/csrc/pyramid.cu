@@ -1,0 +1,170 @@
+// pyramid.cu -- image pyramid, window seeding, winner-take-all and left-right check.
+//
+// Section 3.4 of the paper: the pair is down-sampled by 2 per level; only the top
+// level searches the full range; each finer level searches a per-pixel window whose
+// centre comes from the coarser level's disparities, doubled (the sampling rate), as a
+// block mode at intermediate levels and by linear interpolation at the finest level.
+#include "mpv_internal.cuh"
+
+namespace mpv {
+
+namespace {
+
+__global__ void mirror_kernel(const ImageJob *__restrict__ jobs_unused, ImageJob j0, ImageJob j1,
+                              int W, int H)
+{
+    const ImageJob j = blockIdx.z == 0 ? j0 : j1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    j.dst[(int64_t)y * j.dst_pitch + x] = j.src[(int64_t)y * j.src_pitch + (W - 1 - x)];
+}
+
+struct Jobs4 {
+    ImageJob j[4];
+};
+
+// 2x2 box mean, round half up; the last row/column is replicated when odd.
+__global__ void down2_kernel(Jobs4 jobs, int W, int H)
+{
+    const ImageJob j = jobs.j[blockIdx.z];
+    const int W2 = (W + 1) >> 1, H2 = (H + 1) >> 1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W2 || y >= H2) return;
+    const int x0 = 2 * x, x1 = min(2 * x + 1, W - 1);
+    const int y0 = 2 * y, y1 = min(2 * y + 1, H - 1);
+    const uint8_t *r0 = j.src + (int64_t)y0 * j.src_pitch;
+    const uint8_t *r1 = j.src + (int64_t)y1 * j.src_pitch;
+    const int s = r0[x0] + r0[x1] + r1[x0] + r1[x1];
+    j.dst[(int64_t)y * j.dst_pitch + x] = (uint8_t)((s + 2) >> 2);
+}
+
+__global__ void seed_kernel(SeedArgs a)
+{
+    const int view = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const uint16_t *dp = a.dprev[view];
+    int c;
+    if (a.block >= 2) {
+        // mode of the doubled coarse disparities of the block, ties to the smaller value
+        const int b = a.block;
+        const int qx0 = ((x >> 1) / b) * b, qy0 = ((y >> 1) / b) * b;
+        const int qx1 = min(qx0 + b, a.Wp), qy1 = min(qy0 + b, a.Hp);
+        int best = 0x7FFFFFFF, best_n = 0;
+        for (int qy = qy0; qy < qy1; ++qy)
+            for (int qx = qx0; qx < qx1; ++qx) {
+                const int v = dp[(int64_t)qy * a.Wp + qx];
+                int m = 0;
+                for (int ry = qy0; ry < qy1; ++ry)
+                    for (int rx = qx0; rx < qx1; ++rx) m += (dp[(int64_t)ry * a.Wp + rx] == v);
+                if (m > best_n || (m == best_n && v < best)) {
+                    best = v;
+                    best_n = m;
+                }
+            }
+        c = 2 * best;
+    } else {
+        // each pixel its own block: even positions copy, odd ones take the rounded
+        // mean of their 2 or 4 doubled neighbours (index clamped at the border)
+        const int xa = x >> 1, xb = (x & 1) ? min((x + 1) >> 1, a.Wp - 1) : xa;
+        const int ya = y >> 1, yb = (y & 1) ? min((y + 1) >> 1, a.Hp - 1) : ya;
+        const int nx = (x & 1) ? 2 : 1, ny = (y & 1) ? 2 : 1;
+        int sum = dp[(int64_t)ya * a.Wp + xa];
+        if (nx == 2) sum += dp[(int64_t)ya * a.Wp + xb];
+        if (ny == 2) {
+            sum += dp[(int64_t)yb * a.Wp + xa];
+            if (nx == 2) sum += dp[(int64_t)yb * a.Wp + xb];
+        }
+        const int k = nx * ny;
+        c = (2 * sum + (k >> 1)) / k;
+    }
+    const int lo = min(max(c - (a.Dw >> 1), 0), a.D - a.Dw);
+    a.lo[view][(int64_t)y * a.W + x] = (uint16_t)lo;
+}
+
+// Winner-take-all over each pixel's window, ties to the smallest disparity.
+__global__ void wta_kernel(LevelArgs a)
+{
+    const int view = blockIdx.z;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t npx = (int64_t)a.W * a.H;
+    if (i >= npx) return;
+    const ViewLevel &v = a.v[view];
+    const uint32_t *s = v.S + i * a.Dw;
+    uint32_t best = s[0];
+    int bk = 0;
+    for (int k = 1; k < a.Dw; ++k) {
+        const uint32_t t = s[k];
+        if (t < best) {
+            best = t;
+            bk = k;
+        }
+    }
+    v.d[i] = (uint16_t)((v.lo ? v.lo[i] : 0) + bk);
+}
+
+// Left-right check.  dRm is the right view's map in mirrored coordinates.
+__global__ void lr_kernel(const uint16_t *__restrict__ dL, const uint16_t *__restrict__ dRm,
+                          int W, int H, int tol, int check, uint16_t *out, int out_pitch,
+                          uint16_t *out_right, int right_pitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const int64_t row = (int64_t)y * W;
+    const int d = dL[row + x];
+    uint16_t v = (uint16_t)d;
+    if (check) {
+        v = 0xFFFFu;
+        if (x - d >= 0) {
+            const int dr = dRm[row + (W - 1 - (x - d))];
+            if (abs(d - dr) <= tol) v = (uint16_t)d;
+        }
+    }
+    out[(int64_t)y * out_pitch + x] = v;
+    if (out_right) out_right[(int64_t)y * right_pitch + x] = dRm[row + (W - 1 - x)];
+}
+
+}  // namespace
+
+void launch_mirror(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s)
+{
+    dim3 grid((W + 127) / 128, H, njobs);
+    mirror_kernel<<<grid, 128, 0, s>>>(nullptr, jobs[0], njobs > 1 ? jobs[1] : jobs[0], W, H);
+}
+
+void launch_down2(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s)
+{
+    Jobs4 j4;
+    for (int i = 0; i < 4; ++i) j4.j[i] = jobs[i < njobs ? i : 0];
+    const int W2 = (W + 1) / 2, H2 = (H + 1) / 2;
+    dim3 grid((W2 + 127) / 128, H2, njobs);
+    down2_kernel<<<grid, 128, 0, s>>>(j4, W, H);
+}
+
+void launch_seed(const SeedArgs &a, cudaStream_t s)
+{
+    dim3 grid((a.W + 127) / 128, a.H, a.nviews);
+    seed_kernel<<<grid, 128, 0, s>>>(a);
+}
+
+void launch_wta(const LevelArgs &a, cudaStream_t s)
+{
+    const int64_t npx = (int64_t)a.W * a.H;
+    dim3 grid((unsigned)((npx + 255) / 256), 1, a.nviews);
+    wta_kernel<<<grid, 256, 0, s>>>(a);
+}
+
+void launch_lr(const uint16_t *dL, const uint16_t *dRm, int W, int H, int tol, int check,
+               uint16_t *out, int out_pitch, uint16_t *out_right, int right_pitch,
+               cudaStream_t s)
+{
+    dim3 grid((W + 127) / 128, H, 1);
+    lr_kernel<<<grid, 128, 0, s>>>(dL, dRm, W, H, tol, check, out, out_pitch, out_right,
+                                    right_pitch);
+}
+
+}  // namespace mpv

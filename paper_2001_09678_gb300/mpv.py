@@ -1,0 +1,288 @@
+"""Python binding of the matcher's C ABI (include/mpv.h), by ctypes.
+
+Argument marshalling only: every step of the matcher runs in libmpv.so's CUDA kernels.
+Device tensors are torch tensors (uint8 images, uint16 maps stored in int16/uint16
+tensors), streams are torch CUDA streams.  If the library is missing the import of
+this module fails loudly: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpv.so")
+
+MPV_OK = 0
+MPV_ERR_INVALID_ARG = 1
+MPV_ERR_UNSUPPORTED = 2
+MPV_ERR_OOM = 3
+MPV_ERR_CUDA = 4
+MPV_ERR_TIMEOUT = 5
+MPV_ERR_INTERNAL = 6
+MPV_INVALID = 0xFFFF
+MPV_NO_TRUNC = 0x7FFFFFFF
+MPV_MERGE_SUM = 0
+MPV_PROPOSAL_PYRAMID = 0
+MPV_PROPOSAL_LEARNED = 1
+
+
+class MpvError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {mpv_status_string(status)} ({status})")
+
+
+class mpv_params(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32),
+        ("max_disparity", C.c_int32),
+        ("num_scales", C.c_int32),
+        ("num_paths", C.c_int32),
+        ("p1", C.c_int32),
+        ("trunc", C.c_int32),
+        ("ssim_window", C.c_int32),
+        ("window", C.c_int32),
+        ("block", C.c_int32 * 4),
+        ("lr_check", C.c_int32),
+        ("lr_tol", C.c_int32),
+        ("merge_mode", C.c_int32),
+        ("proposal", C.c_int32),
+    ]
+
+
+class mpv_pair(C.Structure):
+    _fields_ = [
+        ("left", C.c_void_p),
+        ("right", C.c_void_p),
+        ("width", C.c_int32),
+        ("height", C.c_int32),
+        ("pitch", C.c_int32),
+        ("max_disparity", C.c_int32),
+        ("disp", C.c_void_p),
+        ("disp_pitch", C.c_int32),
+        ("disp_right", C.c_void_p),
+    ]
+
+
+EXPORTS = [
+    "mpv_default_params", "mpv_create", "mpv_set_params", "mpv_get_params", "mpv_match",
+    "mpv_match_host", "mpv_match_batch", "mpv_load_proposal_weights", "mpv_sync",
+    "mpv_workspace_bytes", "mpv_set_workspace_limit", "mpv_debug_stage", "mpv_level_info",
+    "mpv_status_string", "mpv_destroy", "mpv_profile_enable", "mpv_profile_read",
+]
+MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libmpv.so (built by paper_2001_09678_gb300.build) and declares its symbols."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmpv.so not built at {path}; run paper_2001_09678_gb300/build.py")
+    L = C.CDLL(path)
+    vp, i32, ctx = C.c_void_p, C.c_int32, C.c_void_p
+    pp = C.POINTER(mpv_params)
+    L.mpv_default_params.argtypes = [pp]
+    L.mpv_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+    L.mpv_set_params.argtypes = [ctx, pp]
+    L.mpv_get_params.argtypes = [ctx, pp]
+    L.mpv_match.argtypes = [ctx, vp, vp, i32, i32, i32, vp, i32, vp]
+    L.mpv_match_host.argtypes = [ctx, vp, vp, i32, i32, i32, vp, i32, vp]
+    L.mpv_match_batch.argtypes = [ctx, C.POINTER(mpv_pair), i32, vp]
+    L.mpv_load_proposal_weights.argtypes = [ctx, C.c_char_p]
+    L.mpv_sync.argtypes = [ctx]
+    L.mpv_workspace_bytes.argtypes = [ctx, i32, i32, C.POINTER(C.c_size_t)]
+    L.mpv_set_workspace_limit.argtypes = [ctx, C.c_size_t]
+    L.mpv_debug_stage.argtypes = [ctx, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp]
+    L.mpv_level_info.argtypes = [ctx, i32, i32, i32] + [C.POINTER(i32)] * 4
+    L.mpv_status_string.argtypes = [C.c_int]
+    L.mpv_status_string.restype = C.c_char_p
+    L.mpv_profile_enable.argtypes = [ctx, i32]
+    L.mpv_profile_read.argtypes = [ctx, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
+    L.mpv_destroy.argtypes = [ctx]
+    L.mpv_destroy.restype = None
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if name not in ("mpv_status_string", "mpv_destroy"):
+            f.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st, what):
+    if st != MPV_OK:
+        raise MpvError(st, what)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---- C ABI, one Python function per entry point ----------------------------------
+
+def mpv_status_string(status: int) -> str:
+    return load().mpv_status_string(status).decode()
+
+
+def mpv_default_params(**overrides) -> mpv_params:
+    p = mpv_params()
+    _check(load().mpv_default_params(C.byref(p)), "mpv_default_params")
+    for k, v in overrides.items():
+        if k == "block":
+            blk = list(v) + [0] * (4 - len(v))
+            for i in range(4):
+                p.block[i] = blk[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def mpv_create(device: int = 0) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().mpv_create(device, C.byref(h)), "mpv_create")
+    return h
+
+
+def mpv_set_params(ctx, p: mpv_params) -> None:
+    _check(load().mpv_set_params(ctx, C.byref(p)), "mpv_set_params")
+
+
+def mpv_get_params(ctx) -> mpv_params:
+    p = mpv_params()
+    _check(load().mpv_get_params(ctx, C.byref(p)), "mpv_get_params")
+    return p
+
+
+def mpv_match(ctx, left, right, disp, stream=None) -> None:
+    """left, right: uint8 CUDA tensors [H, W] (rows may be padded); disp: 16-bit [H, W']."""
+    H, W = left.shape[-2], left.shape[-1]
+    _check(load().mpv_match(ctx, _ptr(left), _ptr(right), W, H, left.stride(-2), _ptr(disp),
+                            disp.stride(-2), _stream(stream)), "mpv_match")
+
+
+def mpv_match_host(ctx, left, right, disp, stream=None) -> None:
+    """Host (CPU) tensors or numpy arrays; copies in and out inside the call."""
+    def addr(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+    def rowstride(a):
+        return a.stride(-2) if hasattr(a, "data_ptr") else a.strides[-2] // a.itemsize
+
+    H, W = left.shape[-2], left.shape[-1]
+    _check(load().mpv_match_host(ctx, C.c_void_p(addr(left)), C.c_void_p(addr(right)), W, H,
+                                 rowstride(left), C.c_void_p(addr(disp)), rowstride(disp),
+                                 _stream(stream)), "mpv_match_host")
+
+
+def mpv_match_batch(ctx, pairs, stream=None) -> None:
+    """pairs: list of dicts with left, right, disp tensors and optional max_disparity,
+    disp_right."""
+    arr = (mpv_pair * len(pairs))()
+    for i, q in enumerate(pairs):
+        left = q["left"]
+        arr[i].left = left.data_ptr()
+        arr[i].right = q["right"].data_ptr()
+        arr[i].height, arr[i].width = left.shape[-2], left.shape[-1]
+        arr[i].pitch = left.stride(-2)
+        arr[i].max_disparity = q.get("max_disparity", 0)
+        arr[i].disp = q["disp"].data_ptr()
+        arr[i].disp_pitch = q["disp"].stride(-2)
+        dr = q.get("disp_right")
+        arr[i].disp_right = dr.data_ptr() if dr is not None else None
+    _check(load().mpv_match_batch(ctx, arr, len(pairs), _stream(stream)), "mpv_match_batch")
+
+
+def mpv_load_proposal_weights(ctx, path: str) -> None:
+    _check(load().mpv_load_proposal_weights(ctx, path.encode()), "mpv_load_proposal_weights")
+
+
+def mpv_sync(ctx) -> None:
+    _check(load().mpv_sync(ctx), "mpv_sync")
+
+
+def mpv_workspace_bytes(ctx, width: int, height: int) -> int:
+    n = C.c_size_t()
+    _check(load().mpv_workspace_bytes(ctx, width, height, C.byref(n)), "mpv_workspace_bytes")
+    return n.value
+
+
+def mpv_set_workspace_limit(ctx, nbytes: int) -> None:
+    _check(load().mpv_set_workspace_limit(ctx, nbytes), "mpv_set_workspace_limit")
+
+
+def mpv_debug_stage(ctx, left, right, view, level, lo=None, cost=None, sum_=None, disp=None,
+                    stream=None) -> None:
+    H, W = left.shape[-2], left.shape[-1]
+    _check(load().mpv_debug_stage(ctx, _ptr(left), _ptr(right), W, H, left.stride(-2), view,
+                                  level, _ptr(lo), _ptr(cost), _ptr(sum_), _ptr(disp),
+                                  _stream(stream)), "mpv_debug_stage")
+
+
+def mpv_level_info(ctx, width: int, height: int, level: int):
+    w, h, r, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().mpv_level_info(ctx, width, height, level, C.byref(w), C.byref(h), C.byref(r),
+                                 C.byref(d)), "mpv_level_info")
+    return w.value, h.value, r.value, d.value
+
+
+def mpv_profile_enable(ctx, on: bool) -> None:
+    _check(load().mpv_profile_enable(ctx, int(bool(on))), "mpv_profile_enable")
+
+
+def mpv_profile_read(ctx):
+    """{stage: (milliseconds, launches)} accumulated since the previous read."""
+    n = len(MPV_STAGES)
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    _check(load().mpv_profile_read(ctx, ms, cnt, n), "mpv_profile_read")
+    return {MPV_STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def mpv_destroy(ctx) -> None:
+    load().mpv_destroy(ctx)
+
+
+class Matcher:
+    """Owns one context; convenience wrapper over the functions above."""
+
+    def __init__(self, device: int = 0, **params):
+        self.ctx = mpv_create(device)
+        self.set_params(**params)
+
+    def set_params(self, **params):
+        self.params = mpv_default_params(**params)
+        mpv_set_params(self.ctx, self.params)
+
+    def match(self, left, right, disp=None, stream=None):
+        import torch
+        if disp is None:
+            disp = torch.empty(left.shape[-2:], dtype=torch.int16, device=left.device)
+        mpv_match(self.ctx, left, right, disp, stream)
+        return disp
+
+    def sync(self):
+        mpv_sync(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            mpv_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
