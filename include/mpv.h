@@ -169,6 +169,34 @@ mpv_status mpv_profile_enable(mpv_ctx *ctx, int32_t on);
  * and resets both.  Either array may be NULL.                                        */
 mpv_status mpv_profile_read(mpv_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 
+/* ---- Matching without device allocation (the paper has no counterpart) -----------
+ *
+ * Some callers cannot call cudaMalloc: a host framework that owns a fixed device pool,
+ * a real-time loop that must not allocate once running, a plug-in inside a process
+ * whose device memory is budgeted by someone else.  mpv_match_noalloc runs the same
+ * matcher as mpv_match with every scratch buffer taken from one fixed array of
+ * MPV_NOALLOC_SCRATCH_BYTES in device global memory, declared in the library itself:
+ * every GPU that loads the library holds that array until the process exits.  The call
+ * allocates nothing (no cudaMalloc, no cudaFree, no allocating library routine) and
+ * needs no context; the caller still owns the images and the output.
+ *   - Uses the device that is current on the calling thread.  The first call on a
+ *     device looks up the array's device address (cudaGetSymbolAddress); make that
+ *     first call before any stream capture.
+ *   - A pair whose scratch need exceeds MPV_NOALLOC_SCRATCH_BYTES is rejected with
+ *     MPV_ERR_INVALID_ARG before anything is launched (640 x 480 at D = 64 with three
+ *     scales and the left-right check fits; 1280 x 720 at D = 128 does not).  The
+ *     learned proposal and the right-view output are not available here.
+ *   - Every call shares the one array, which keeps the previous call's contents (the
+ *     call clears what must start at zero).  Calls that overlap on the GPU (other
+ *     streams, other threads) race on it: serialize them on one stream.
+ * Arguments as for mpv_match, plus the parameters to use (validated as by
+ * mpv_set_params).                                                                     */
+#define MPV_NOALLOC_SCRATCH_BYTES (64u << 20)
+mpv_status mpv_match_noalloc(const mpv_params *params, const uint8_t *left,
+                             const uint8_t *right, int32_t width, int32_t height,
+                             int32_t pitch, uint16_t *disp, int32_t disp_pitch,
+                             void *cuda_stream);
+
 const char *mpv_status_string(mpv_status s);
 
 /* Releases the context and its workspace; NULL is accepted. */

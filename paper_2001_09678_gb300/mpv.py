@@ -70,7 +70,9 @@ EXPORTS = [
     "mpv_match_host", "mpv_match_batch", "mpv_load_proposal_weights", "mpv_sync",
     "mpv_workspace_bytes", "mpv_set_workspace_limit", "mpv_debug_stage", "mpv_level_info",
     "mpv_status_string", "mpv_destroy", "mpv_profile_enable", "mpv_profile_read",
+    "mpv_match_noalloc",
 ]
+MPV_NOALLOC_SCRATCH_BYTES = 64 << 20
 MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
 
 _lib = None
@@ -103,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.mpv_status_string.restype = C.c_char_p
     L.mpv_profile_enable.argtypes = [ctx, i32]
     L.mpv_profile_read.argtypes = [ctx, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
+    L.mpv_match_noalloc.argtypes = [pp, vp, vp, i32, i32, i32, vp, i32, vp]
     L.mpv_destroy.argtypes = [ctx]
     L.mpv_destroy.restype = None
     for name in EXPORTS:
@@ -249,6 +252,15 @@ def mpv_profile_read(ctx):
     cnt = (C.c_int64 * n)()
     _check(load().mpv_profile_read(ctx, ms, cnt, n), "mpv_profile_read")
     return {MPV_STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def mpv_match_noalloc(params: mpv_params, left, right, disp, stream=None) -> None:
+    """The matcher with all scratch in the library's fixed device array (no allocation);
+    see include/mpv.h for its size limit and its sharing rules."""
+    H, W = left.shape[-2], left.shape[-1]
+    _check(load().mpv_match_noalloc(C.byref(params), _ptr(left), _ptr(right), W, H,
+                                    left.stride(-2), _ptr(disp), disp.stride(-2),
+                                    _stream(stream)), "mpv_match_noalloc")
 
 
 def mpv_destroy(ctx) -> None:
