@@ -1,36 +1,39 @@
 // aggregate.cu -- directional Viterbi passes summed over 4 or 8 scan directions.
 //
-// Section 3.2 / Eq. e(p,u): along each scan direction r the energy of node (p,u) is
-// its cost plus the cheapest predecessor node (p-r, v) plus the jump penalty
-// eps(u,v) = min(p1 |u-v|, T), with every node of the predecessor connected (full
+// Section 3.2 / Eq. e(p,u): along each scan direction r the energy of node (p,u) is its
+// cost plus the cheapest predecessor node (p-r, v) plus the jump penalty
+// eps(u,v) = min(p1 |u-v|, T), every node of the predecessor connected (full
 // connectivity).  Section 3.3 evaluates that minimum in O(2m) by one upward and one
-// downward sweep over the labels.  Here the two sweeps are written as prefix minima:
-//     min_{v<=u} A(v) + p1 (u - v) = p1 u + min_{v<=u} (A(v) - p1 v)
-//     min_{v>=u} A(v) + p1 (v - u) = -p1 u + min_{v>=u} (A(v) + p1 v)
-// so a warp evaluates them as two shuffle scans over its lanes.  Labels are absolute
-// disparities: a predecessor with a different window start connects through the
-// penalty, and labels outside its window are virtual nodes (absent).  Energies are
-// kept in the bounded form L = C + M' - min_v A(v) (a per-pixel constant shift that
-// leaves every argmin unchanged), and each pass adds L into the summed volume S.
+// downward sweep over the labels.  Labels are absolute disparities: a predecessor with a
+// different window start connects through the penalty, and labels outside its window
+// are virtual nodes (absent).  Energies are kept in the bounded form
+//     L(p,u) = C(p,u) + M'(u) - min_v L(p-r,v),   M'(u) = min_v L(p-r,v) + eps(u,v),
+// a per-pixel constant shift of the literal recursion that leaves every argmin unchanged
+// and keeps every value below 8192; each pass adds L into the summed volume S.
 //
-// v1 layout: one warp per scan path, K = ceil(Dw/32) consecutive labels per lane.
+// Two kernels:
+//  * agg_stencil: when the truncation makes every jump of more than R labels cost T
+//    (R = ceil(T/p1) - 1 <= 4; the default p1 = 10, T = 30 gives R = 2), the two sweeps
+//    reduce to  M'(u) = min(min_{|d|<=R} L(p-r,u+d) + p1|d|, min_v L(p-r,v) + T).
+//    Four lanes own one scan path, each lane 2*KW consecutive labels packed two per
+//    32-bit register; the stencil is packed 16-bit add-min arithmetic, the halo words
+//    come from the neighbouring lanes by shuffles, and a window shift between
+//    consecutive pixels (pyramid levels) re-indexes the predecessor through shared
+//    memory.  S is accumulated with 64-bit reductions of four packed labels.
+//  * agg_scan: any R and window width: one warp per scan path, the two sweeps written
+//    as prefix minima  min_{v<=u} A(v) + p1 (u-v) = p1 u + min_{v<=u} (A(v) - p1 v)
+//    (and the mirror image), evaluated by shuffle scans over the lanes.
 #include "mpv_internal.cuh"
 
 namespace mpv {
 
 namespace {
 
-constexpr int kWarps = 8;
-
 __constant__ int c_dirs[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1},
                                  {1, 1}, {-1, -1}, {-1, 1}, {1, -1}};
 
-__device__ __forceinline__ int warp_min(int v)
-{
-    return __reduce_min_sync(0xFFFFFFFFu, v);
-}
+constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Start pixel and number of paths of direction (dx,dy) on a W x H level.
 __device__ __forceinline__ int num_paths_dir(int dx, int dy, int W, int H)
 {
     if (dy == 0) return H;
@@ -38,6 +41,8 @@ __device__ __forceinline__ int num_paths_dir(int dx, int dy, int W, int H)
     return W + H - 1;
 }
 
+// First pixel of path i of direction (dx,dy): the pixels whose predecessor p - r lies
+// outside the image.
 __device__ __forceinline__ void path_start(int dx, int dy, int W, int H, int i, int &x, int &y)
 {
     if (dy == 0) {
@@ -55,16 +60,205 @@ __device__ __forceinline__ void path_start(int dx, int dy, int W, int H, int i, 
     }
 }
 
+// ---------------------------------------------------------------------------------
+// agg_stencil
+// ---------------------------------------------------------------------------------
+
+constexpr int kG = 4;                       // lanes per scan path
+constexpr int kStencilWarps = 4;            // warps per block
+constexpr int kPathsPerWarp = 32 / kG;
+
+// (high half of a, low half of b): the word of labels shifted by one
+__device__ __forceinline__ uint32_t shift1(uint32_t a, uint32_t b)
+{
+    return __byte_perm(a, b, 0x5432);
+}
+
+template <int KW, int R>
+__global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
+{
+    constexpr int HW = (R + 1) / 2;          // halo words per side
+    constexpr int NE = KW + 2 * HW;          // words with halos
+    constexpr int K = 2 * KW;                // labels per lane
+    constexpr int DWP = kG * K;              // labels per path (= the volume stride)
+    constexpr int PAD = DWP + 4 * HW;        // absent labels around a re-indexed path
+    constexpr int BUF = 2 * PAD + DWP;
+
+    __shared__ __align__(16) uint16_t rbuf[kStencilWarps][kPathsPerWarp][BUF];
+
+    const int view = blockIdx.z, dir = blockIdx.y;
+    const int dx = c_dirs[dir][0], dy = c_dirs[dir][1];
+    const int W = a.W, H = a.H, Dw = a.Dw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane & (kG - 1), grp = lane >> 2;
+    const unsigned gmask = 0xFu << (grp * 4);
+    const int path = (blockIdx.x * kStencilWarps + warp) * kPathsPerWarp + grp;
+    const ViewLevel &V = a.v[view];
+
+    uint16_t *gb = rbuf[warp][grp];
+    for (int i = gl; i < BUF; i += kG) gb[i] = (uint16_t)kInf16;
+    __syncwarp();
+
+    const uint32_t INF2 = kInf16 * 0x10001u;
+    const uint32_t Tx2 = (uint32_t)a.trunc * 0x10001u;
+    const uint32_t P1x2 = (uint32_t)a.p1 * 0x10001u;
+    const uint32_t P2x2 = 2u * P1x2, P3x2 = 3u * P1x2, P4x2 = 4u * P1x2;
+
+    // labels at or beyond Dw are padding: never a predecessor, never summed
+    const bool padded = Dw < DWP;
+    uint32_t keep[KW];
+#pragma unroll
+    for (int i = 0; i < KW; ++i) {
+        const int k0 = gl * K + 2 * i;
+        keep[i] = (k0 < Dw ? 0x0000FFFFu : 0u) | (k0 + 1 < Dw ? 0xFFFF0000u : 0u);
+    }
+
+    int x = 0, y = 0;
+    bool inside = path < num_paths_dir(dx, dy, W, H);
+    if (inside) path_start(dx, dy, W, H, path, x, y);
+    uint32_t A[KW];
+#pragma unroll
+    for (int i = 0; i < KW; ++i) A[i] = INF2;   // no predecessor: L = C at the first pixel
+    int prev_lo = -1;
+
+    while (__any_sync(kFull, inside)) {
+        int64_t pix = 0;
+        int cur_lo = 0;
+        uint32_t c[KW];
+        if (inside) {
+            pix = (int64_t)y * W + x;
+            cur_lo = V.lo ? (int)V.lo[pix] : 0;
+            const uint32_t *cp = (const uint32_t *)(V.C + pix * DWP + gl * K);
+#pragma unroll
+            for (int j = 0; j < KW / 2; ++j) {
+                const uint32_t q = __ldg(cp + j);
+                c[2 * j] = __byte_perm(q, 0u, 0x4140);
+                c[2 * j + 1] = __byte_perm(q, 0u, 0x4342);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < KW; ++i) c[i] = 0u;
+        }
+
+        // minimum of the predecessor over the path's four lanes
+        uint32_t m2 = A[0];
+#pragma unroll
+        for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
+        uint32_t mm = min(m2 & 0xFFFFu, m2 >> 16);
+        mm = min(mm, __shfl_xor_sync(kFull, mm, 1));
+        mm = min(mm, __shfl_xor_sync(kFull, mm, 2));
+        const uint32_t minA2 = mm * 0x10001u;
+        const uint32_t cap = minA2 + Tx2;
+
+        // predecessor words with HW halo words on each side
+        uint32_t E[NE];
+#pragma unroll
+        for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
+#pragma unroll
+        for (int h = 0; h < HW; ++h) {
+            const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
+            const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
+            E[h] = gl == 0 ? INF2 : l;
+            E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
+        }
+        const int s = cur_lo - prev_lo;          // window shift, uniform over the path
+        if (inside && prev_lo >= 0 && s != 0) {
+            uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
+#pragma unroll
+            for (int i = 0; i < KW; ++i) gw[i] = A[i];
+            __syncwarp(gmask);
+            const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
+            const int j0 = PAD + gl * K - 2 * HW + sc;
+#pragma unroll
+            for (int w = 0; w < NE; ++w)
+                E[w] = (uint32_t)gb[j0 + 2 * w] | ((uint32_t)gb[j0 + 2 * w + 1] << 16);
+            __syncwarp(gmask);
+        }
+
+        uint32_t SH[NE - 1];
+#pragma unroll
+        for (int j = 0; j < NE - 1; ++j) SH[j] = shift1(E[j], E[j + 1]);
+
+#pragma unroll
+        for (int i = 0; i < KW; ++i) {
+            const int e = HW + i;
+            uint32_t m = __vminu2(E[e], cap);
+            if (R >= 1) {
+                m = __viaddmin_u16x2(SH[e - 1], P1x2, m);
+                m = __viaddmin_u16x2(SH[e], P1x2, m);
+            }
+            if (R >= 2) {
+                m = __viaddmin_u16x2(E[e - 1], P2x2, m);
+                m = __viaddmin_u16x2(E[e + 1], P2x2, m);
+            }
+            if (R >= 3) {
+                m = __viaddmin_u16x2(SH[e - 2], P3x2, m);
+                m = __viaddmin_u16x2(SH[e + 1], P3x2, m);
+            }
+            if (R >= 4) {
+                m = __viaddmin_u16x2(E[e - 2], P4x2, m);
+                m = __viaddmin_u16x2(E[e + 2], P4x2, m);
+            }
+            uint32_t L = c[i] + m - minA2;      // per-half: no carry, no borrow
+            if (padded) {
+                L &= keep[i];
+                A[i] = L | (INF2 & ~keep[i]);
+            } else {
+                A[i] = L;
+            }
+            c[i] = L;
+        }
+        if (inside) {
+            unsigned long long *sp =
+                (unsigned long long *)(V.S + pix * DWP + gl * K);
+#pragma unroll
+            for (int j = 0; j < KW / 2; ++j)
+                atomicAdd(sp + j, ((unsigned long long)c[2 * j + 1] << 32) | c[2 * j]);
+        }
+        prev_lo = cur_lo;
+        x += dx;
+        y += dy;
+        inside = inside && x >= 0 && x < W && y >= 0 && y < H;
+    }
+}
+
+template <int KW, int R>
+void launch_stencil(const LevelArgs &a, cudaStream_t s)
+{
+    const int maxp = a.W + a.H - 1;
+    const int per_block = kStencilWarps * kPathsPerWarp;
+    dim3 grid((maxp + per_block - 1) / per_block, a.npaths, a.nviews);
+    agg_stencil<KW, R><<<grid, kStencilWarps * 32, 0, s>>>(a);
+}
+
+template <int KW>
+void launch_stencil_r(const LevelArgs &a, cudaStream_t s)
+{
+    switch (a.radius) {
+    case 0: launch_stencil<KW, 0>(a, s); break;
+    case 1: launch_stencil<KW, 1>(a, s); break;
+    case 2: launch_stencil<KW, 2>(a, s); break;
+    case 3: launch_stencil<KW, 3>(a, s); break;
+    default: launch_stencil<KW, 4>(a, s); break;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// agg_scan (general radius and width)
+// ---------------------------------------------------------------------------------
+
+constexpr int kScanWarps = 8;
+
 template <int K>
-__global__ void __launch_bounds__(kWarps * 32) aggregate_kernel(LevelArgs a)
+__global__ void __launch_bounds__(kScanWarps * 32) agg_scan(LevelArgs a)
 {
     const int view = blockIdx.z;
     const int dir = blockIdx.y;
     const int dx = c_dirs[dir][0], dy = c_dirs[dir][1];
-    const int W = a.W, H = a.H, Dw = a.Dw;
+    const int W = a.W, H = a.H, Dw = a.Dw, Dws = a.Dws;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int path = blockIdx.x * kWarps + warp;
+    const int path = blockIdx.x * kScanWarps + warp;
     if (path >= num_paths_dir(dx, dy, W, H)) return;
     const ViewLevel &V = a.v[view];
     const int P1 = a.p1, T = a.trunc;
@@ -76,18 +270,19 @@ __global__ void __launch_bounds__(kWarps * 32) aggregate_kernel(LevelArgs a)
     int x, y;
     path_start(dx, dy, W, H, path, x, y);
     int A[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) A[t] = kInf;
     int prev_lo = 0;
     bool first = true;
     while (x >= 0 && x < W && y >= 0 && y < H) {
         const int64_t pix = (int64_t)y * W + x;
         const int cur_lo = V.lo ? (int)V.lo[pix] : 0;
-        const uint16_t *cp = V.C + pix * Dw;
-        uint32_t *sp = V.S + pix * Dw;
+        const uint8_t *cp = V.C + pix * Dws;
         int c[K];
 #pragma unroll
         for (int t = 0; t < K; ++t) {
             const int k = lane * K + t;
-            c[t] = k < Dw ? (int)cp[k] : kInf;
+            c[t] = k < Dw ? (int)cp[k] : 0;
         }
         int L[K];
         if (first) {
@@ -95,11 +290,10 @@ __global__ void __launch_bounds__(kWarps * 32) aggregate_kernel(LevelArgs a)
             for (int t = 0; t < K; ++t) L[t] = c[t];
             first = false;
         } else {
-            // minimum of the predecessor and the two scans
             int m = A[0];
 #pragma unroll
             for (int t = 1; t < K; ++t) m = min(m, A[t]);
-            const int amin = warp_min(m);
+            const int amin = __reduce_min_sync(kFull, m);
             int pb[K], sc[K];
             int run = kInf;
 #pragma unroll
@@ -110,10 +304,10 @@ __global__ void __launch_bounds__(kWarps * 32) aggregate_kernel(LevelArgs a)
             int incl = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                const int v = __shfl_up_sync(kFull, incl, o);
                 if (lane >= o) incl = min(incl, v);
             }
-            int excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+            int excl = __shfl_up_sync(kFull, incl, 1);
             if (lane == 0) excl = kInf;
 #pragma unroll
             for (int t = 0; t < K; ++t) pb[t] = min(pb[t], excl);
@@ -126,10 +320,10 @@ __global__ void __launch_bounds__(kWarps * 32) aggregate_kernel(LevelArgs a)
             incl = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_down_sync(0xFFFFFFFFu, incl, o);
+                const int v = __shfl_down_sync(kFull, incl, o);
                 if (lane + o < 32) incl = min(incl, v);
             }
-            excl = __shfl_down_sync(0xFFFFFFFFu, incl, 1);
+            excl = __shfl_down_sync(kFull, incl, 1);
             if (lane == 31) excl = kInf;
 #pragma unroll
             for (int t = 0; t < K; ++t) sc[t] = min(sc[t], excl);
@@ -164,15 +358,30 @@ __global__ void __launch_bounds__(kWarps * 32) aggregate_kernel(LevelArgs a)
                 }
                 __syncwarp();
             }
+        }
+        // S: packed 16-bit pairs, padding labels add nothing
 #pragma unroll
-            for (int t = 0; t < K; ++t)
-                if (lane * K + t >= Dw) L[t] = kInf;
+        for (int t = 0; t < K; ++t) {
+            const int k = lane * K + t;
+            if (k >= Dw) L[t] = 0;
+        }
+        uint16_t *sp = V.S + pix * Dws;
+        if (K == 1) {
+            const int up = __shfl_down_sync(kFull, L[0], 1);
+            if ((lane & 1) == 0 && lane < Dws)
+                atomicAdd((unsigned int *)(sp + lane), (unsigned)L[0] | ((unsigned)up << 16));
+        } else {
+#pragma unroll
+            for (int t = 0; t < K; t += 2) {
+                const int k = lane * K + t;
+                if (k < Dws)
+                    atomicAdd((unsigned int *)(sp + k), (unsigned)L[t] | ((unsigned)L[t + 1] << 16));
+            }
         }
 #pragma unroll
         for (int t = 0; t < K; ++t) {
             const int k = lane * K + t;
-            if (k < Dw) atomicAdd(sp + k, (uint32_t)L[t]);
-            A[t] = L[t];
+            A[t] = k < Dw ? L[t] : kInf;
         }
         prev_lo = cur_lo;
         x += dx;
@@ -181,27 +390,34 @@ __global__ void __launch_bounds__(kWarps * 32) aggregate_kernel(LevelArgs a)
 }
 
 template <int K>
-void launch_k(const LevelArgs &a, cudaStream_t s)
+void launch_scan(const LevelArgs &a, cudaStream_t s)
 {
     const int maxp = a.W + a.H - 1;
-    dim3 grid((maxp + kWarps - 1) / kWarps, a.npaths, a.nviews);
-    const size_t smem = sizeof(int) * kWarps * 2 * (32 * K + 2);
-    cudaFuncSetAttribute(aggregate_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    aggregate_kernel<K><<<grid, kWarps * 32, smem, s>>>(a);
+    dim3 grid((maxp + kScanWarps - 1) / kScanWarps, a.npaths, a.nviews);
+    const size_t smem = sizeof(int) * kScanWarps * 2 * (32 * K + 2);
+    cudaFuncSetAttribute(agg_scan<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    agg_scan<K><<<grid, kScanWarps * 32, smem, s>>>(a);
 }
 
 }  // namespace
 
 void launch_aggregate(const LevelArgs &a, cudaStream_t s)
 {
+    if (a.radius <= 4 && a.Dws <= 64) {
+        switch (a.Dws / 8) {
+        case 2: launch_stencil_r<2>(a, s); return;
+        case 4: launch_stencil_r<4>(a, s); return;
+        case 6: launch_stencil_r<6>(a, s); return;
+        default: launch_stencil_r<8>(a, s); return;
+        }
+    }
     const int K = (a.Dw + 31) / 32;
-    if (K <= 1) launch_k<1>(a, s);
-    else if (K <= 2) launch_k<2>(a, s);
-    else if (K <= 4) launch_k<4>(a, s);
-    else if (K <= 8) launch_k<8>(a, s);
-    else if (K <= 16) launch_k<16>(a, s);
-    else launch_k<32>(a, s);
+    if (K <= 1) launch_scan<1>(a, s);
+    else if (K <= 2) launch_scan<2>(a, s);
+    else if (K <= 4) launch_scan<4>(a, s);
+    else if (K <= 8) launch_scan<8>(a, s);
+    else if (K <= 16) launch_scan<16>(a, s);
+    else launch_scan<32>(a, s);
 }
 
 }  // namespace mpv

@@ -25,10 +25,6 @@ constexpr int TX = 32;       // pixels per tile
 constexpr int UCAP = 256;    // widest disparity span handled with shared column products
 constexpr int kThreads = 256;
 
-struct CostSmem {
-    int tile_w, wb, ucap;
-};
-
 // Floor of 255 (den - num) / (2 den) for |num| <= den, den > 0, exactly.
 // fp32 estimate: A1, A2, B1, B2 are integers below 2^27 in magnitude, so each
 // conversion and product carries relative error <= 2^-24, the quotient <= 2 ulp; the
@@ -165,38 +161,42 @@ __global__ void __launch_bounds__(kThreads) cost_kernel(LevelArgs a)
     __syncthreads();
 
     const int c1 = a.c1, c2 = a.c2;
-    uint16_t *out = V.C + ((int64_t)y * W + x0) * Dw;
-    const int total = nx * Dw;
-    for (int e = tid; e < total; e += kThreads) {
-        const int i = e / Dw, k = e - i * Dw;
+    const int Dws = a.Dws;
+    const int lane = tid & 31, warp = tid >> 5;
+    // one warp per pixel, lanes over labels: the pixel's Dws cost bytes are contiguous
+    for (int i = warp; i < nx; i += kThreads / 32) {
+        uint8_t *out = V.C + ((int64_t)y * W + x0 + i) * Dws;
         const int lo = lo_s[i];
-        const int u = lo + k;
-        const int xp = x0 + i - u;
-        int q = 255;
-        if (xp >= 0) {
-            int sxy = 0;
-            if (use_cp) {
-                const int *row = cp_s + (lo - minlo + k) * CPW + i;
+        const int sx = sx_s[i], sxq = sxq_s[i], vx = vx_s[i];
+        for (int k = lane; k < Dws; k += 32) {
+            const int u = lo + k;
+            const int xp = x0 + i - u;
+            int q = 255;
+            if (k < Dw && xp >= 0) {
+                int sxy = 0;
+                if (use_cp) {
+                    const int *row = cp_s + (lo - minlo + k) * CPW + i;
 #pragma unroll
-                for (int dx = 0; dx < N; ++dx) sxy += row[dx];
-            } else {
-                const int b0 = xp - R - bmin;
+                    for (int dx = 0; dx < N; ++dx) sxy += row[dx];
+                } else {
+                    const int b0 = xp - R - bmin;
 #pragma unroll
-                for (int dy = 0; dy < N; ++dy)
+                    for (int dy = 0; dy < N; ++dy)
 #pragma unroll
-                    for (int dx = 0; dx < N; ++dx)
-                        sxy += (int)i0_s[dy][i + dx] * (int)i1_s[dy * WB + b0 + dx];
+                        for (int dx = 0; dx < N; ++dx)
+                            sxy += (int)i0_s[dy][i + dx] * (int)i1_s[dy * WB + b0 + dx];
+                }
+                const int cc = xp - R - bmin;           // I1 centre index
+                const int sy = sy_s[cc];
+                const int sxsy = sx * sy;
+                const int A1 = 2 * sxsy + c1;
+                const int B1 = sxq + syq_s[cc] + c1;
+                const int A2 = 2 * (n * sxy - sxsy) + c2;
+                const int B2 = vx + vy_s[cc] + c2;
+                q = ssim_quotient(A1, A2, B1, B2);
             }
-            const int cc = xp - R - bmin;               // I1 centre index
-            const int sx = sx_s[i], sy = sy_s[cc];
-            const int sxsy = sx * sy;
-            const int A1 = 2 * sxsy + c1;
-            const int B1 = sxq_s[i] + syq_s[cc] + c1;
-            const int A2 = 2 * (n * sxy - sxsy) + c2;
-            const int B2 = vx_s[i] + vy_s[cc] + c2;
-            q = ssim_quotient(A1, A2, B1, B2);
+            out[k] = (uint8_t)q;
         }
-        out[e] = (uint16_t)q;
     }
 }
 

@@ -5,7 +5,6 @@
 #include <new>
 #include <vector>
 
-#include "../../include/mpv.h"
 #include "mpv_internal.cuh"
 
 using namespace mpv;
@@ -32,125 +31,6 @@ struct mpv_ctx {
 };
 
 namespace {
-
-struct Geometry {
-    int S;
-    int W[kMaxScales], H[kMaxScales], D[kMaxScales], Dw[kMaxScales], block[kMaxScales];
-    int pitch[kMaxScales];  // workspace image pitch per level
-};
-
-int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-
-int ssim_c1(int N)
-{
-    const int64_t n = (int64_t)N * N;
-    return (int)((65025 * n * n + 5000) / 10000);   // (0.01*255)^2 * n^2, rounded
-}
-
-int ssim_c2(int N)
-{
-    const int64_t n = (int64_t)N * N;
-    return (int)((585225 * n * n + 5000) / 10000);  // (0.03*255)^2 * n^2, rounded
-}
-
-bool params_valid(const mpv_params &p)
-{
-    if (p.struct_size != sizeof(mpv_params)) return false;
-    if (p.ssim_window != 3 && p.ssim_window != 5) return false;
-    if (p.num_scales < 1 || p.num_scales > kMaxScales) return false;
-    if (p.num_paths != 4 && p.num_paths != 8) return false;
-    if (p.max_disparity < 1 || p.max_disparity > 1024) return false;
-    if (p.p1 < 0 || p.trunc < 0 || p.window < 0 || p.lr_tol < 0) return false;
-    if (p.lr_check != 0 && p.lr_check != 1) return false;
-    if (p.merge_mode != MPV_MERGE_SUM) return false;
-    if (p.proposal != MPV_PROPOSAL_PYRAMID && p.proposal != MPV_PROPOSAL_LEARNED) return false;
-    for (int i = 0; i < 4; ++i)
-        if (p.block[i] < 0 || p.block[i] > 8) return false;
-    return true;
-}
-
-// Level sizes, ranges and windows (Section 3.4): level S-1 is the input, each level
-// above halves the size (rounding up) and the range; the top level searches its
-// whole range, the others a window of Dw labels (D/4 by default).
-bool geometry(const mpv_params &p, int W, int H, int D, Geometry &g)
-{
-    g.S = p.num_scales;
-    int w = W, h = H;
-    for (int l = g.S - 1; l >= 0; --l) {
-        g.W[l] = w;
-        g.H[l] = h;
-        const int sh = g.S - 1 - l;
-        g.D[l] = (D + (1 << sh) - 1) >> sh;
-        w = (w + 1) / 2;
-        h = (h + 1) / 2;
-    }
-    int Dw = p.window > 0 ? p.window : D / 4;
-    if (Dw < 1) Dw = 1;
-    for (int l = 0; l < g.S; ++l) {
-        g.Dw[l] = l == 0 ? g.D[0] : (Dw < g.D[l] ? Dw : g.D[l]);
-        const int b = l > 0 ? p.block[l - 1] : 0;
-        g.block[l] = b > 0 ? b : (l == g.S - 1 ? 1 : 2);
-        g.pitch[l] = (int)ceil_div(g.W[l], 16) * 16;
-    }
-    return true;
-}
-
-mpv_status validate_pair(const mpv_params &p, int W, int H, int pitch, int disp_pitch, int D)
-{
-    const int N = p.ssim_window;
-    if (W < N || H < N) return MPV_ERR_INVALID_ARG;
-    if (D < 1 || D > W || D > 1024) return MPV_ERR_INVALID_ARG;
-    if (pitch < W || disp_pitch < W) return MPV_ERR_INVALID_ARG;
-    Geometry g;
-    geometry(p, W, H, D, g);
-    if (g.W[0] < N || g.H[0] < N) return MPV_ERR_INVALID_ARG;
-    const int64_t jump = (int64_t)p.p1 * (D - 1);
-    const int64_t pen = p.trunc < jump ? p.trunc : jump;
-    if ((int64_t)p.num_paths * (255 + pen) >= 65535) return MPV_ERR_INVALID_ARG;
-    if ((int64_t)W * H > (int64_t)1 << 27) return MPV_ERR_UNSUPPORTED;
-    if (p.proposal == MPV_PROPOSAL_LEARNED) return MPV_ERR_UNSUPPORTED;
-    return MPV_OK;
-}
-
-// Workspace layout of one pair.
-struct Layout {
-    size_t total = 0;
-    size_t img0[kMaxViews][kMaxScales], img1[kMaxViews][kMaxScales];
-    size_t lo[kMaxViews][kMaxScales], d[kMaxViews][kMaxScales];
-    size_t C[kMaxViews], S[kMaxViews];
-};
-
-size_t take(size_t &off, size_t bytes)
-{
-    const size_t at = off;
-    off += (bytes + 255) & ~(size_t)255;
-    return at;
-}
-
-Layout layout(const Geometry &g, int nviews)
-{
-    Layout L;
-    size_t off = 0;
-    int64_t maxvol = 0;
-    for (int l = 0; l < g.S; ++l) {
-        const int64_t v = (int64_t)g.W[l] * g.H[l] * g.Dw[l];
-        if (v > maxvol) maxvol = v;
-    }
-    for (int v = 0; v < nviews; ++v) {
-        for (int l = 0; l < g.S; ++l) {
-            const size_t img = (size_t)g.pitch[l] * g.H[l];
-            const bool caller = (v == 0 && l == g.S - 1);
-            L.img0[v][l] = caller ? 0 : take(off, img);
-            L.img1[v][l] = caller ? 0 : take(off, img);
-            L.lo[v][l] = take(off, sizeof(uint16_t) * (size_t)g.W[l] * g.H[l]);
-            L.d[v][l] = take(off, sizeof(uint16_t) * (size_t)g.W[l] * g.H[l]);
-        }
-        L.C[v] = take(off, sizeof(uint16_t) * (size_t)maxvol);
-        L.S[v] = take(off, sizeof(uint32_t) * (size_t)maxvol);
-    }
-    L.total = off;
-    return L;
-}
 
 mpv_status cuda_status(cudaError_t e)
 {
@@ -180,21 +60,6 @@ mpv_status ensure_workspace(mpv_ctx *ctx, size_t bytes)
     return MPV_OK;
 }
 
-struct Job {
-    const uint8_t *left, *right;
-    int W, H, pitch, D;
-    uint16_t *disp;
-    int disp_pitch;
-    uint16_t *disp_right;
-};
-
-// Stage sink for mpv_debug_stage.
-struct StageOut {
-    int view = -1, level = -1;
-    uint16_t *lo = nullptr, *cost = nullptr, *disp = nullptr;
-    uint32_t *sum = nullptr;
-};
-
 cudaEvent_t pool_event(mpv_ctx *ctx)
 {
     if (!ctx->pool.empty()) {
@@ -207,145 +72,34 @@ cudaEvent_t pool_event(mpv_ctx *ctx)
     return e;
 }
 
-// Runs `launch` (which enqueues `nkernels` kernels on s) under the profiler.
-template <class F>
-void stage(mpv_ctx *ctx, int which, int nkernels, cudaStream_t s, F &&launch)
+void hook_begin(void *user, int stage, int nkernels, cudaStream_t s)
 {
-    ctx->launches[which] += nkernels;
-    if (!ctx->profiling) {
-        launch();
-        return;
-    }
-    mpv_ctx::Rec r{which, pool_event(ctx), pool_event(ctx)};
+    mpv_ctx *ctx = (mpv_ctx *)user;
+    ctx->launches[stage] += nkernels;
+    if (!ctx->profiling) return;
+    mpv_ctx::Rec r{stage, pool_event(ctx), pool_event(ctx)};
     cudaEventRecord(r.a, s);
-    launch();
-    cudaEventRecord(r.b, s);
     ctx->recs.push_back(r);
 }
 
-// Enqueues the whole matcher for one pair on stream s.
-mpv_status enqueue_pair(mpv_ctx *ctx, const Job &job, cudaStream_t s, const StageOut *dbg)
+void hook_end(void *user, int stage, cudaStream_t s)
 {
-    const mpv_params &p = ctx->p;
+    mpv_ctx *ctx = (mpv_ctx *)user;
+    (void)stage;
+    if (!ctx->profiling || ctx->recs.empty()) return;
+    cudaEventRecord(ctx->recs.back().b, s);
+}
+
+// Enqueues one pair with the context's workspace and profiler.
+mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const StageSink *dbg)
+{
     Geometry g;
-    geometry(p, job.W, job.H, job.D, g);
-    const bool need_right = p.lr_check || job.disp_right || (dbg && dbg->view == 1);
-    const int nviews = need_right ? 2 : 1;
-    const Layout L = layout(g, nviews);
-    mpv_status st = ensure_workspace(ctx, L.total);
+    make_geometry(ctx->p, job.W, job.H, job.D, g);
+    const Layout L = make_layout(g, views_needed(ctx->p, job, dbg));
+    const mpv_status st = ensure_workspace(ctx, L.total);
     if (st != MPV_OK) return st;
-    uint8_t *base = (uint8_t *)ctx->ws;
-    const int S = g.S;
-    const int top = S - 1;
-
-    auto img0 = [&](int v, int l) -> uint8_t * { return base + L.img0[v][l]; };
-    auto img1 = [&](int v, int l) -> uint8_t * { return base + L.img1[v][l]; };
-
-    const uint8_t *I0[kMaxViews][kMaxScales];
-    const uint8_t *I1[kMaxViews][kMaxScales];
-    int P0[kMaxViews][kMaxScales], P1[kMaxViews][kMaxScales];
-    for (int v = 0; v < nviews; ++v)
-        for (int l = 0; l < S; ++l) {
-            I0[v][l] = img0(v, l);
-            I1[v][l] = img1(v, l);
-            P0[v][l] = P1[v][l] = g.pitch[l];
-        }
-    I0[0][top] = job.left;
-    I1[0][top] = job.right;
-    P0[0][top] = P1[0][top] = job.pitch;
-
-    // right view: the mirrored, swapped pair
-    if (nviews == 2) {
-        ImageJob m[2] = {{job.right, job.pitch, img0(1, top), g.pitch[top]},
-                         {job.left, job.pitch, img1(1, top), g.pitch[top]}};
-        stage(ctx, MPV_STAGE_PYRAMID, 1, s, [&] { launch_mirror(m, 2, job.W, job.H, s); });
-    }
-    // pyramid
-    for (int l = top - 1; l >= 0; --l) {
-        ImageJob jobs[4];
-        int n = 0;
-        for (int v = 0; v < nviews; ++v) {
-            jobs[n++] = {I0[v][l + 1], P0[v][l + 1], img0(v, l), g.pitch[l]};
-            jobs[n++] = {I1[v][l + 1], P1[v][l + 1], img1(v, l), g.pitch[l]};
-        }
-        stage(ctx, MPV_STAGE_PYRAMID, 1, s,
-              [&] { launch_down2(jobs, n, g.W[l + 1], g.H[l + 1], s); });
-    }
-
-    const int Teff = p.trunc >= MPV_NO_TRUNC ? kInf : p.trunc;
-    const int P1eff = p.trunc >= MPV_NO_TRUNC ? p.p1 : (p.p1 < p.trunc ? p.p1 : p.trunc);
-    const int last = dbg ? dbg->level : top;
-    for (int l = 0; l <= last; ++l) {
-        LevelArgs a{};
-        a.W = g.W[l];
-        a.H = g.H[l];
-        a.D = g.D[l];
-        a.Dw = g.Dw[l];
-        a.nviews = nviews;
-        a.N = p.ssim_window;
-        a.c1 = ssim_c1(a.N);
-        a.c2 = ssim_c2(a.N);
-        a.p1 = P1eff;
-        a.trunc = Teff;
-        a.npaths = p.num_paths;
-        for (int v = 0; v < nviews; ++v) {
-            ViewLevel &vl = a.v[v];
-            vl.I0 = I0[v][l];
-            vl.I1 = I1[v][l];
-            vl.pitch0 = P0[v][l];
-            vl.pitch1 = P1[v][l];
-            vl.lo = l == 0 ? nullptr : (const uint16_t *)(base + L.lo[v][l]);
-            vl.C = (uint16_t *)(base + L.C[v]);
-            vl.S = (uint32_t *)(base + L.S[v]);
-            vl.d = (uint16_t *)(base + L.d[v][l]);
-        }
-        if (l > 0) {
-            SeedArgs sa{};
-            sa.W = g.W[l];
-            sa.H = g.H[l];
-            sa.Wp = g.W[l - 1];
-            sa.Hp = g.H[l - 1];
-            sa.block = g.block[l];
-            sa.Dw = g.Dw[l];
-            sa.D = g.D[l];
-            sa.nviews = nviews;
-            for (int v = 0; v < nviews; ++v) {
-                sa.dprev[v] = (const uint16_t *)(base + L.d[v][l - 1]);
-                sa.lo[v] = (uint16_t *)(base + L.lo[v][l]);
-            }
-            stage(ctx, MPV_STAGE_SEED, 1, s, [&] { launch_seed(sa, s); });
-        }
-        stage(ctx, MPV_STAGE_COST, 1, s, [&] { launch_cost(a, s); });
-        const size_t vol = (size_t)a.W * a.H * a.Dw;
-        stage(ctx, MPV_STAGE_AGGREGATE, 1, s, [&] {
-            for (int v = 0; v < nviews; ++v)
-                cudaMemsetAsync(a.v[v].S, 0, vol * sizeof(uint32_t), s);
-            launch_aggregate(a, s);
-        });
-        stage(ctx, MPV_STAGE_WTA, 1, s, [&] { launch_wta(a, s); });
-        if (dbg && l == dbg->level) {
-            const ViewLevel &vl = a.v[dbg->view];
-            const size_t npx = (size_t)a.W * a.H;
-            if (dbg->lo) {
-                if (vl.lo)
-                    cudaMemcpyAsync(dbg->lo, vl.lo, npx * 2, cudaMemcpyDeviceToDevice, s);
-                else
-                    cudaMemsetAsync(dbg->lo, 0, npx * 2, s);
-            }
-            if (dbg->cost) cudaMemcpyAsync(dbg->cost, vl.C, vol * 2, cudaMemcpyDeviceToDevice, s);
-            if (dbg->sum) cudaMemcpyAsync(dbg->sum, vl.S, vol * 4, cudaMemcpyDeviceToDevice, s);
-            if (dbg->disp) cudaMemcpyAsync(dbg->disp, vl.d, npx * 2, cudaMemcpyDeviceToDevice, s);
-        }
-    }
-    if (!dbg) {
-        const uint16_t *dL = (const uint16_t *)(base + L.d[0][top]);
-        const uint16_t *dRm = nviews == 2 ? (const uint16_t *)(base + L.d[1][top]) : dL;
-        stage(ctx, MPV_STAGE_LR, 1, s, [&] {
-            launch_lr(dL, dRm, job.W, job.H, p.lr_tol, p.lr_check, job.disp, job.disp_pitch,
-                      nviews == 2 ? job.disp_right : nullptr, job.disp_pitch, s);
-        });
-    }
-    return cuda_status(cudaGetLastError());
+    StageHook hook{hook_begin, hook_end, ctx};
+    return enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg);
 }
 
 struct DeviceGuard {
@@ -456,10 +210,10 @@ mpv_status mpv_match_batch(mpv_ctx *ctx, const mpv_pair *pairs, int32_t n, void 
     ctx->last_stream = s;
     for (int i = 0; i < n; ++i) {
         const mpv_pair &q = pairs[i];
-        Job j{q.left, q.right, q.width, q.height, q.pitch,
-              q.max_disparity > 0 ? q.max_disparity : ctx->p.max_disparity,
-              q.disp, q.disp_pitch, q.disp_right};
-        const mpv_status st = enqueue_pair(ctx, j, s, nullptr);
+        PairJob j{q.left, q.right, q.width, q.height, q.pitch,
+                  q.max_disparity > 0 ? q.max_disparity : ctx->p.max_disparity,
+                  q.disp, q.disp_pitch, q.disp_right};
+        const mpv_status st = enqueue(ctx, j, s, nullptr);
         if (st != MPV_OK) return st;
     }
     return MPV_OK;
@@ -526,8 +280,8 @@ mpv_status mpv_workspace_bytes(const mpv_ctx *ctx, int32_t width, int32_t height
 {
     if (!ctx || !bytes || width < 1 || height < 1) return MPV_ERR_INVALID_ARG;
     Geometry g;
-    geometry(ctx->p, width, height, ctx->p.max_disparity, g);
-    *bytes = layout(g, ctx->p.lr_check ? 2 : 1).total;
+    make_geometry(ctx->p, width, height, ctx->p.max_disparity, g);
+    *bytes = make_layout(g, ctx->p.lr_check ? 2 : 1).total;
     return MPV_OK;
 }
 
@@ -551,15 +305,15 @@ mpv_status mpv_debug_stage(mpv_ctx *ctx, const uint8_t *left, const uint8_t *rig
     if (st != MPV_OK) return st;
     DeviceGuard guard(ctx->device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    StageOut dbg;
+    StageSink dbg;
     dbg.view = view;
     dbg.level = level;
     dbg.lo = lo;
     dbg.cost = cost;
     dbg.sum = sum;
     dbg.disp = disp;
-    Job j{left, right, width, height, pitch, ctx->p.max_disparity, nullptr, width, nullptr};
-    mpv_status r = enqueue_pair(ctx, j, s, &dbg);
+    PairJob j{left, right, width, height, pitch, ctx->p.max_disparity, nullptr, width, nullptr};
+    mpv_status r = enqueue(ctx, j, s, &dbg);
     if (r != MPV_OK) return r;
     return cuda_status(cudaStreamSynchronize(s));
 }
@@ -570,7 +324,7 @@ mpv_status mpv_level_info(const mpv_ctx *ctx, int32_t width, int32_t height, int
     if (!ctx || level < 0 || level >= ctx->p.num_scales || width < 1 || height < 1)
         return MPV_ERR_INVALID_ARG;
     Geometry g;
-    geometry(ctx->p, width, height, ctx->p.max_disparity, g);
+    make_geometry(ctx->p, width, height, ctx->p.max_disparity, g);
     if (w) *w = g.W[level];
     if (h) *h = g.H[level];
     if (range) *range = g.D[level];

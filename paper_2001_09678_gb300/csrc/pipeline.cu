@@ -1,0 +1,262 @@
+// pipeline.cu -- validation, pyramid geometry, workspace layout and the launch sequence
+// of one stereo pair, shared by every entry point of the C ABI.
+#include "mpv_internal.cuh"
+
+namespace mpv {
+
+namespace {
+
+int ssim_c1(int N)
+{
+    const int64_t n = (int64_t)N * N;
+    return (int)((65025 * n * n + 5000) / 10000);   // (0.01*255)^2 * n^2, rounded
+}
+
+int ssim_c2(int N)
+{
+    const int64_t n = (int64_t)N * N;
+    return (int)((585225 * n * n + 5000) / 10000);  // (0.03*255)^2 * n^2, rounded
+}
+
+size_t take(size_t &off, size_t bytes)
+{
+    const size_t at = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return at;
+}
+
+struct HookScope {
+    const StageHook *h;
+    int stage;
+    cudaStream_t s;
+    HookScope(const StageHook *h_, int stage_, int nk, cudaStream_t s_) : h(h_), stage(stage_), s(s_)
+    {
+        if (h && h->begin) h->begin(h->user, stage, nk, s);
+    }
+    ~HookScope()
+    {
+        if (h && h->end) h->end(h->user, stage, s);
+    }
+};
+
+}  // namespace
+
+bool params_valid(const mpv_params &p)
+{
+    if (p.struct_size != sizeof(mpv_params)) return false;
+    if (p.ssim_window != 3 && p.ssim_window != 5) return false;
+    if (p.num_scales < 1 || p.num_scales > kMaxScales) return false;
+    if (p.num_paths != 4 && p.num_paths != 8) return false;
+    if (p.max_disparity < 1 || p.max_disparity > 1024) return false;
+    if (p.p1 < 0 || p.trunc < 0 || p.window < 0 || p.lr_tol < 0) return false;
+    if (p.lr_check != 0 && p.lr_check != 1) return false;
+    if (p.merge_mode != MPV_MERGE_SUM) return false;
+    if (p.proposal != MPV_PROPOSAL_PYRAMID && p.proposal != MPV_PROPOSAL_LEARNED) return false;
+    for (int i = 0; i < 4; ++i)
+        if (p.block[i] < 0 || p.block[i] > 8) return false;
+    return true;
+}
+
+// Level sizes, ranges and windows (Section 3.4): level S-1 is the input, each level
+// above halves the size (rounding up) and the range; the top level searches its whole
+// range, the others a window of Dw labels (D/4 by default).
+void make_geometry(const mpv_params &p, int W, int H, int D, Geometry &g)
+{
+    g.S = p.num_scales;
+    int w = W, h = H;
+    for (int l = g.S - 1; l >= 0; --l) {
+        g.W[l] = w;
+        g.H[l] = h;
+        const int sh = g.S - 1 - l;
+        g.D[l] = (D + (1 << sh) - 1) >> sh;
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+    }
+    int Dw = p.window > 0 ? p.window : D / 4;
+    if (Dw < 1) Dw = 1;
+    for (int l = 0; l < g.S; ++l) {
+        g.Dw[l] = l == 0 ? g.D[0] : (Dw < g.D[l] ? Dw : g.D[l]);
+        g.Dws[l] = (g.Dw[l] + 15) / 16 * 16;
+        const int b = l > 0 ? p.block[l - 1] : 0;
+        g.block[l] = b > 0 ? b : (l == g.S - 1 ? 1 : 2);
+        g.pitch[l] = (g.W[l] + 15) / 16 * 16;
+    }
+}
+
+mpv_status validate_pair(const mpv_params &p, int W, int H, int pitch, int disp_pitch, int D)
+{
+    const int N = p.ssim_window;
+    if (W < N || H < N) return MPV_ERR_INVALID_ARG;
+    if (D < 1 || D > W || D > 1024) return MPV_ERR_INVALID_ARG;
+    if (pitch < W || disp_pitch < W) return MPV_ERR_INVALID_ARG;
+    Geometry g;
+    make_geometry(p, W, H, D, g);
+    if (g.W[0] < N || g.H[0] < N) return MPV_ERR_INVALID_ARG;
+    const int64_t jump = (int64_t)p.p1 * (D - 1);
+    const int64_t pen = p.trunc < jump ? p.trunc : jump;
+    if ((int64_t)p.num_paths * (255 + pen) >= 65535) return MPV_ERR_INVALID_ARG;
+    if ((int64_t)W * H > (int64_t)1 << 27) return MPV_ERR_UNSUPPORTED;
+    if (p.proposal == MPV_PROPOSAL_LEARNED) return MPV_ERR_UNSUPPORTED;
+    return MPV_OK;
+}
+
+Layout make_layout(const Geometry &g, int nviews)
+{
+    Layout L;
+    size_t off = 0;
+    int64_t maxvol = 0;
+    for (int l = 0; l < g.S; ++l) {
+        const int64_t v = (int64_t)g.W[l] * g.H[l] * g.Dws[l];
+        if (v > maxvol) maxvol = v;
+    }
+    for (int v = 0; v < nviews; ++v) {
+        for (int l = 0; l < g.S; ++l) {
+            const size_t img = (size_t)g.pitch[l] * g.H[l];
+            const bool caller = (v == 0 && l == g.S - 1);
+            L.img0[v][l] = caller ? 0 : take(off, img);
+            L.img1[v][l] = caller ? 0 : take(off, img);
+            L.lo[v][l] = take(off, sizeof(uint16_t) * (size_t)g.W[l] * g.H[l]);
+            L.d[v][l] = take(off, sizeof(uint16_t) * (size_t)g.W[l] * g.H[l]);
+        }
+        L.C[v] = take(off, sizeof(uint8_t) * (size_t)maxvol);
+        L.S[v] = take(off, sizeof(uint16_t) * (size_t)maxvol);
+    }
+    L.total = off;
+    return L;
+}
+
+int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg)
+{
+    return (p.lr_check || job.disp_right || (dbg && dbg->view == 1)) ? 2 : 1;
+}
+
+mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, cudaStream_t s,
+                        const StageHook *hook, const StageSink *dbg)
+{
+    Geometry g;
+    make_geometry(p, job.W, job.H, job.D, g);
+    const int nviews = views_needed(p, job, dbg);
+    const Layout L = make_layout(g, nviews);
+    const int S = g.S;
+    const int top = S - 1;
+
+    const uint8_t *I0[kMaxViews][kMaxScales];
+    const uint8_t *I1[kMaxViews][kMaxScales];
+    int P0[kMaxViews][kMaxScales], P1[kMaxViews][kMaxScales];
+    for (int v = 0; v < nviews; ++v)
+        for (int l = 0; l < S; ++l) {
+            I0[v][l] = base + L.img0[v][l];
+            I1[v][l] = base + L.img1[v][l];
+            P0[v][l] = P1[v][l] = g.pitch[l];
+        }
+    I0[0][top] = job.left;
+    I1[0][top] = job.right;
+    P0[0][top] = P1[0][top] = job.pitch;
+
+    // right view: the mirrored, swapped pair
+    if (nviews == 2) {
+        HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
+        ImageJob m[2] = {{job.right, job.pitch, base + L.img0[1][top], g.pitch[top]},
+                         {job.left, job.pitch, base + L.img1[1][top], g.pitch[top]}};
+        launch_mirror(m, 2, job.W, job.H, s);
+    }
+    for (int l = top - 1; l >= 0; --l) {
+        HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
+        ImageJob jobs[4];
+        int n = 0;
+        for (int v = 0; v < nviews; ++v) {
+            jobs[n++] = {I0[v][l + 1], P0[v][l + 1], base + L.img0[v][l], g.pitch[l]};
+            jobs[n++] = {I1[v][l + 1], P1[v][l + 1], base + L.img1[v][l], g.pitch[l]};
+        }
+        launch_down2(jobs, n, g.W[l + 1], g.H[l + 1], s);
+    }
+
+    const int last = dbg ? dbg->level : top;
+    for (int l = 0; l <= last; ++l) {
+        LevelArgs a{};
+        a.W = g.W[l];
+        a.H = g.H[l];
+        a.D = g.D[l];
+        a.Dw = g.Dw[l];
+        a.Dws = g.Dws[l];
+        a.nviews = nviews;
+        a.N = p.ssim_window;
+        a.c1 = ssim_c1(a.N);
+        a.c2 = ssim_c2(a.N);
+        // penalty min(p1 |du|, T) over labels of one level: |du| <= D_l - 1, so a
+        // truncation above p1 (D_l - 1) never acts and p1 above T acts as T
+        const int64_t span = (int64_t)p.p1 * (g.D[l] - 1);
+        const int64_t Teff = (int64_t)p.trunc < span ? p.trunc : span;
+        a.trunc = (int)Teff;
+        a.p1 = (int)(p.p1 < Teff ? p.p1 : Teff);
+        a.radius = a.p1 > 0 ? (int)((Teff + a.p1 - 1) / a.p1) - 1 : 0;
+        a.npaths = p.num_paths;
+        for (int v = 0; v < nviews; ++v) {
+            ViewLevel &vl = a.v[v];
+            vl.I0 = I0[v][l];
+            vl.I1 = I1[v][l];
+            vl.pitch0 = P0[v][l];
+            vl.pitch1 = P1[v][l];
+            vl.lo = l == 0 ? nullptr : (const uint16_t *)(base + L.lo[v][l]);
+            vl.C = base + L.C[v];
+            vl.S = (uint16_t *)(base + L.S[v]);
+            vl.d = (uint16_t *)(base + L.d[v][l]);
+        }
+        if (l > 0) {
+            HookScope hs(hook, MPV_STAGE_SEED, 1, s);
+            SeedArgs sa{};
+            sa.W = g.W[l];
+            sa.H = g.H[l];
+            sa.Wp = g.W[l - 1];
+            sa.Hp = g.H[l - 1];
+            sa.block = g.block[l];
+            sa.Dw = g.Dw[l];
+            sa.D = g.D[l];
+            sa.nviews = nviews;
+            for (int v = 0; v < nviews; ++v) {
+                sa.dprev[v] = (const uint16_t *)(base + L.d[v][l - 1]);
+                sa.lo[v] = (uint16_t *)(base + L.lo[v][l]);
+            }
+            launch_seed(sa, s);
+        }
+        {
+            HookScope hs(hook, MPV_STAGE_COST, 1, s);
+            launch_cost(a, s);
+        }
+        {
+            HookScope hs(hook, MPV_STAGE_AGGREGATE, 1, s);
+            const size_t vol = (size_t)a.W * a.H * a.Dws;
+            for (int v = 0; v < nviews; ++v)
+                cudaMemsetAsync(a.v[v].S, 0, vol * sizeof(uint16_t), s);
+            launch_aggregate(a, s);
+        }
+        {
+            HookScope hs(hook, MPV_STAGE_WTA, 1, s);
+            launch_wta(a, s);
+        }
+        if (dbg && l == dbg->level) {
+            const ViewLevel &vl = a.v[dbg->view];
+            const size_t npx = (size_t)a.W * a.H;
+            if (dbg->lo) {
+                if (vl.lo)
+                    cudaMemcpyAsync(dbg->lo, vl.lo, npx * 2, cudaMemcpyDeviceToDevice, s);
+                else
+                    cudaMemsetAsync(dbg->lo, 0, npx * 2, s);
+            }
+            if (dbg->cost || dbg->sum) launch_unpack(a, dbg->view, dbg->cost, dbg->sum, s);
+            if (dbg->disp) cudaMemcpyAsync(dbg->disp, vl.d, npx * 2, cudaMemcpyDeviceToDevice, s);
+        }
+    }
+    if (!dbg) {
+        HookScope hs(hook, MPV_STAGE_LR, 1, s);
+        const uint16_t *dL = (const uint16_t *)(base + L.d[0][top]);
+        const uint16_t *dRm = nviews == 2 ? (const uint16_t *)(base + L.d[1][top]) : dL;
+        launch_lr(dL, dRm, job.W, job.H, p.lr_tol, p.lr_check, job.disp, job.disp_pitch,
+                  nviews == 2 ? job.disp_right : nullptr, job.disp_pitch, s);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return MPV_OK;
+    return e == cudaErrorMemoryAllocation ? MPV_ERR_OOM : MPV_ERR_CUDA;
+}
+
+}  // namespace mpv

@@ -85,25 +85,41 @@ __global__ void seed_kernel(SeedArgs a)
     a.lo[view][(int64_t)y * a.W + x] = (uint16_t)lo;
 }
 
-// Winner-take-all over each pixel's window, ties to the smallest disparity.
+// Winner-take-all over each pixel's window, ties to the smallest disparity.  Four lanes
+// per pixel; the key (S << 16 | k) orders by energy, then by label.
 __global__ void wta_kernel(LevelArgs a)
 {
     const int view = blockIdx.z;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = g >> 2;
+    const int sub = (int)(g & 3);
     const int64_t npx = (int64_t)a.W * a.H;
-    if (i >= npx) return;
+    const bool in = i < npx;
     const ViewLevel &v = a.v[view];
-    const uint32_t *s = v.S + i * a.Dw;
-    uint32_t best = s[0];
-    int bk = 0;
-    for (int k = 1; k < a.Dw; ++k) {
-        const uint32_t t = s[k];
-        if (t < best) {
-            best = t;
-            bk = k;
+    uint32_t best = 0xFFFFFFFFu;
+    if (in) {
+        const uint16_t *s = v.S + i * a.Dws;
+        for (int k = sub; k < a.Dw; k += 4) {
+            const uint32_t key = ((uint32_t)s[k] << 16) | (uint32_t)k;
+            best = min(best, key);
         }
     }
-    v.d[i] = (uint16_t)((v.lo ? v.lo[i] : 0) + bk);
+    best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 1));
+    best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 2));
+    if (in && sub == 0) v.d[i] = (uint16_t)((v.lo ? v.lo[i] : 0) + (best & 0xFFFFu));
+}
+
+// Stage dump: C and S in the documented [H][W][Dw] layout (u16 and u32).
+__global__ void unpack_kernel(LevelArgs a, int view, uint16_t *cost, uint32_t *sum)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)a.W * a.H * a.Dw;
+    if (e >= n) return;
+    const int64_t pix = e / a.Dw;
+    const int k = (int)(e - pix * a.Dw);
+    const ViewLevel &v = a.v[view];
+    if (cost) cost[e] = v.C[pix * a.Dws + k];
+    if (sum) sum[e] = v.S[pix * a.Dws + k];
 }
 
 // Left-right check.  dRm is the right view's map in mirrored coordinates.
@@ -153,9 +169,15 @@ void launch_seed(const SeedArgs &a, cudaStream_t s)
 
 void launch_wta(const LevelArgs &a, cudaStream_t s)
 {
-    const int64_t npx = (int64_t)a.W * a.H;
-    dim3 grid((unsigned)((npx + 255) / 256), 1, a.nviews);
+    const int64_t nthreads = 4 * (int64_t)a.W * a.H;
+    dim3 grid((unsigned)((nthreads + 255) / 256), 1, a.nviews);
     wta_kernel<<<grid, 256, 0, s>>>(a);
+}
+
+void launch_unpack(const LevelArgs &a, int view, uint16_t *cost, uint32_t *sum, cudaStream_t s)
+{
+    const int64_t n = (int64_t)a.W * a.H * a.Dw;
+    unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, view, cost, sum);
 }
 
 void launch_lr(const uint16_t *dL, const uint16_t *dRm, int W, int H, int tol, int check,

@@ -87,6 +87,18 @@ CASES = {
                            dict(max_disparity=64, num_scales=3, num_paths=8)),
     "odd_window_17": (lambda: synth.slanted_pair(256, 144, seed=17, d_max=100)[:2],
                       dict(max_disparity=128, num_scales=2, num_paths=8, window=17)),
+    # stencil radius ceil(T/p1) - 1 = 1, 3, 4 (the default p1=10, T=30 gives 2)
+    "radius1": (lambda: synth.slanted_pair(192, 96, seed=18, d_max=40)[:2],
+                dict(max_disparity=48, num_scales=2, num_paths=8, p1=10, trunc=20)),
+    "radius3": (lambda: synth.slanted_pair(192, 96, seed=19, d_max=40)[:2],
+                dict(max_disparity=48, num_scales=2, num_paths=8, p1=10, trunc=40)),
+    "radius4_t45": (lambda: synth.slanted_pair(192, 96, seed=20, d_max=40)[:2],
+                    dict(max_disparity=48, num_scales=3, num_paths=8, p1=10, trunc=45)),
+    # packed widths: 48 labels (top level of D=192, 3 scales) and 64 labels
+    "dw48_s3": (lambda: synth.slanted_pair(400, 120, seed=22, d_max=180)[:2],
+                dict(max_disparity=192, num_scales=3, num_paths=8)),
+    "dw64_s1": (lambda: synth.bands_pair(200, 60, seed=23, disparities=(10, 30, 55))[:2],
+                dict(max_disparity=64, num_scales=1, num_paths=8)),
 }
 
 
