@@ -68,41 +68,80 @@ constexpr int kG = 4;                       // lanes per scan path
 constexpr int kStencilWarps = 4;            // warps per block
 constexpr int kPathsPerWarp = 32 / kG;
 
+// Prefetch loads of the scan paths.  Written as volatile asm so that the compiler keeps
+// them where they are issued (PF steps ahead of their use) instead of re-issuing a
+// read-only load next to its use.
+__device__ __forceinline__ uint32_t ld_pin_u32(const void *p)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_pin_u64(const void *p)
+{
+    uint2 v;
+    asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_pin_u16(const void *p)
+{
+    unsigned short v;
+    asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+
 // (high half of a, low half of b): the word of labels shifted by one
 __device__ __forceinline__ uint32_t shift1(uint32_t a, uint32_t b)
 {
     return __byte_perm(a, b, 0x5432);
 }
 
-template <int KW, int R>
+// Number of pixels of the path that starts at (x0,y0) in direction (dx,dy).
+__device__ __forceinline__ int path_length(int dx, int dy, int W, int H, int x0, int y0)
+{
+    const int nx = dx > 0 ? W - x0 : (dx < 0 ? x0 + 1 : 0x7FFFFFFF);
+    const int ny = dy > 0 ? H - y0 : (dy < 0 ? y0 + 1 : 0x7FFFFFFF);
+    return min(nx, ny);
+}
+
+// RM: largest jump |d| handled explicitly.  The penalty of a jump of d labels is
+// eps(d) = min(p1 d, T) for every d <= RM, so whenever the truncation dominates beyond
+// RM (ceil(T/p1) - 1 <= RM) the stencil min over |d| <= RM plus the cap min_v A(v) + T
+// is the full-connectivity minimum.  WIN: the level has per-pixel windows, and the
+// predecessor is re-indexed into the current window through shared memory every step.
+template <int KW, int RM, bool WIN>
 __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
 {
-    constexpr int HW = (R + 1) / 2;          // halo words per side
+    constexpr int HW = RM / 2;               // halo words per side
     constexpr int NE = KW + 2 * HW;          // words with halos
     constexpr int K = 2 * KW;                // labels per lane
     constexpr int DWP = kG * K;              // labels per path (= the volume stride)
-    constexpr int PAD = DWP + 4 * HW;        // absent labels around a re-indexed path
+    constexpr int PAD = (DWP + 4 * HW + 2 + 7) / 8 * 8;  // absent labels around a path
     constexpr int BUF = 2 * PAD + DWP;
+    constexpr int PF = KW <= 4 ? 8 : 4;      // prefetch distance (steps)
+    constexpr int CW = KW / 2;               // 32-bit words of cost bytes per lane
 
-    __shared__ __align__(16) uint16_t rbuf[kStencilWarps][kPathsPerWarp][BUF];
+    __shared__ __align__(16) uint16_t rbuf[WIN ? kStencilWarps * kPathsPerWarp * BUF : 8];
 
     const int view = blockIdx.z, dir = blockIdx.y;
     const int dx = c_dirs[dir][0], dy = c_dirs[dir][1];
     const int W = a.W, H = a.H, Dw = a.Dw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = lane & (kG - 1), grp = lane >> 2;
-    const unsigned gmask = 0xFu << (grp * 4);
     const int path = (blockIdx.x * kStencilWarps + warp) * kPathsPerWarp + grp;
     const ViewLevel &V = a.v[view];
 
-    uint16_t *gb = rbuf[warp][grp];
-    for (int i = gl; i < BUF; i += kG) gb[i] = (uint16_t)kInf16;
-    __syncwarp();
+    uint16_t *gb = rbuf + (WIN ? (warp * kPathsPerWarp + grp) * BUF : 0);
+    if (WIN) {
+        for (int i = gl; i < BUF; i += kG) gb[i] = (uint16_t)kInf16;
+        __syncwarp();
+    }
 
     const uint32_t INF2 = kInf16 * 0x10001u;
-    const uint32_t Tx2 = (uint32_t)a.trunc * 0x10001u;
-    const uint32_t P1x2 = (uint32_t)a.p1 * 0x10001u;
-    const uint32_t P2x2 = 2u * P1x2, P3x2 = 3u * P1x2, P4x2 = 4u * P1x2;
+    const uint32_t T = (uint32_t)a.trunc, P1 = (uint32_t)a.p1;
+    const uint32_t Tx2 = T * 0x10001u;
+    const uint32_t E1 = min(P1, T) * 0x10001u, E2 = min(2 * P1, T) * 0x10001u;
+    const uint32_t E3 = min(3 * P1, T) * 0x10001u, E4 = min(4 * P1, T) * 0x10001u;
 
     // labels at or beyond Dw are padding: never a predecessor, never summed
     const bool padded = Dw < DWP;
@@ -113,133 +152,159 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
         keep[i] = (k0 < Dw ? 0x0000FFFFu : 0u) | (k0 + 1 < Dw ? 0xFFFF0000u : 0u);
     }
 
-    int x = 0, y = 0;
-    bool inside = path < num_paths_dir(dx, dy, W, H);
-    if (inside) path_start(dx, dy, W, H, path, x, y);
+    int x0 = 0, y0 = 0, n = 0;
+    if (path < num_paths_dir(dx, dy, W, H)) {
+        path_start(dx, dy, W, H, path, x0, y0);
+        n = path_length(dx, dy, W, H, x0, y0);
+    }
+    const int nmax = __reduce_max_sync(kFull, n);
+    const int pix0 = y0 * W + x0;
+    const int dpix = dy * W + dx;
+    const uint8_t *cbase = V.C + gl * K;
+    uint16_t *sbase = V.S + gl * K;
+    const uint16_t *lob = V.lo;
+
+    // prefetch ring (registers): cost bytes and window start of the next PF steps
+    uint32_t cq[PF][CW];
+    uint32_t lq[PF];
+    auto issue = [&](int t, int slot) {
+        if (t < n) {
+            const int pix = pix0 + t * dpix;
+            const uint8_t *src = cbase + (int64_t)pix * DWP;
+            if (CW % 2 == 0) {
+#pragma unroll
+                for (int j = 0; j < CW; j += 2) {
+                    const uint2 v = ld_pin_u64(src + 4 * j);
+                    cq[slot][j] = v.x;
+                    cq[slot][j + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < CW; ++j) cq[slot][j] = ld_pin_u32(src + 4 * j);
+            }
+            lq[slot] = WIN ? ld_pin_u16(lob + pix) : 0u;
+        }
+    };
+#pragma unroll
+    for (int u = 0; u < PF; ++u) issue(u, u);
+
     uint32_t A[KW];
 #pragma unroll
     for (int i = 0; i < KW; ++i) A[i] = INF2;   // no predecessor: L = C at the first pixel
     int prev_lo = -1;
 
-    while (__any_sync(kFull, inside)) {
-        int64_t pix = 0;
-        int cur_lo = 0;
-        uint32_t c[KW];
-        if (inside) {
-            pix = (int64_t)y * W + x;
-            cur_lo = V.lo ? (int)V.lo[pix] : 0;
-            const uint32_t *cp = (const uint32_t *)(V.C + pix * DWP + gl * K);
+    for (int t0 = 0; t0 < nmax; t0 += PF) {
 #pragma unroll
-            for (int j = 0; j < KW / 2; ++j) {
-                const uint32_t q = __ldg(cp + j);
-                c[2 * j] = __byte_perm(q, 0u, 0x4140);
-                c[2 * j + 1] = __byte_perm(q, 0u, 0x4342);
+        for (int u = 0; u < PF; ++u) {
+            const int t = t0 + u;
+            if (t >= nmax) break;
+            const bool act = t < n;
+            const int pix = pix0 + t * dpix;
+            uint32_t c[KW];
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+                c[2 * j] = __byte_perm(cq[u][j], 0u, 0x4140);
+                c[2 * j + 1] = __byte_perm(cq[u][j], 0u, 0x4342);
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < KW; ++i) c[i] = 0u;
-        }
+            const int cur_lo = (int)lq[u];
+            issue(t + PF, u);
 
-        // minimum of the predecessor over the path's four lanes
-        uint32_t m2 = A[0];
+            // minimum of the predecessor over the path's lanes, in both halves
+            uint32_t m2 = A[0];
 #pragma unroll
-        for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
-        uint32_t mm = min(m2 & 0xFFFFu, m2 >> 16);
-        mm = min(mm, __shfl_xor_sync(kFull, mm, 1));
-        mm = min(mm, __shfl_xor_sync(kFull, mm, 2));
-        const uint32_t minA2 = mm * 0x10001u;
-        const uint32_t cap = minA2 + Tx2;
+            for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
+            m2 = __vminu2(m2, __byte_perm(m2, m2, 0x1032));
+            m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, 1));
+            m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, 2));
+            const uint32_t cap = m2 + Tx2;
 
-        // predecessor words with HW halo words on each side
-        uint32_t E[NE];
+            // predecessor words around this lane's labels, HW halo words per side
+            uint32_t E[NE];
+            if (WIN) {
+                uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
 #pragma unroll
-        for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
+                for (int i = 0; i < KW; ++i) gw[i] = A[i];
+                __syncwarp();
+                const int s = (act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
+                const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
+                const int j0 = PAD + gl * K - 2 * HW + sc;
+                const uint32_t *gwords = (const uint32_t *)gb + (j0 >> 1);
+                const uint32_t sel = (j0 & 1) ? 0x5432u : 0x3210u;
+                uint32_t Wd[NE + 1];
 #pragma unroll
-        for (int h = 0; h < HW; ++h) {
-            const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
-            const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
-            E[h] = gl == 0 ? INF2 : l;
-            E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
-        }
-        const int s = cur_lo - prev_lo;          // window shift, uniform over the path
-        if (inside && prev_lo >= 0 && s != 0) {
-            uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
+                for (int i = 0; i <= NE; ++i) Wd[i] = gwords[i];
 #pragma unroll
-            for (int i = 0; i < KW; ++i) gw[i] = A[i];
-            __syncwarp(gmask);
-            const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
-            const int j0 = PAD + gl * K - 2 * HW + sc;
-#pragma unroll
-            for (int w = 0; w < NE; ++w)
-                E[w] = (uint32_t)gb[j0 + 2 * w] | ((uint32_t)gb[j0 + 2 * w + 1] << 16);
-            __syncwarp(gmask);
-        }
-
-        uint32_t SH[NE - 1];
-#pragma unroll
-        for (int j = 0; j < NE - 1; ++j) SH[j] = shift1(E[j], E[j + 1]);
-
-#pragma unroll
-        for (int i = 0; i < KW; ++i) {
-            const int e = HW + i;
-            uint32_t m = __vminu2(E[e], cap);
-            if (R >= 1) {
-                m = __viaddmin_u16x2(SH[e - 1], P1x2, m);
-                m = __viaddmin_u16x2(SH[e], P1x2, m);
-            }
-            if (R >= 2) {
-                m = __viaddmin_u16x2(E[e - 1], P2x2, m);
-                m = __viaddmin_u16x2(E[e + 1], P2x2, m);
-            }
-            if (R >= 3) {
-                m = __viaddmin_u16x2(SH[e - 2], P3x2, m);
-                m = __viaddmin_u16x2(SH[e + 1], P3x2, m);
-            }
-            if (R >= 4) {
-                m = __viaddmin_u16x2(E[e - 2], P4x2, m);
-                m = __viaddmin_u16x2(E[e + 2], P4x2, m);
-            }
-            uint32_t L = c[i] + m - minA2;      // per-half: no carry, no borrow
-            if (padded) {
-                L &= keep[i];
-                A[i] = L | (INF2 & ~keep[i]);
+                for (int w = 0; w < NE; ++w) E[w] = __byte_perm(Wd[w], Wd[w + 1], sel);
+                __syncwarp();
             } else {
-                A[i] = L;
-            }
-            c[i] = L;
-        }
-        if (inside) {
-            unsigned long long *sp =
-                (unsigned long long *)(V.S + pix * DWP + gl * K);
 #pragma unroll
-            for (int j = 0; j < KW / 2; ++j)
-                atomicAdd(sp + j, ((unsigned long long)c[2 * j + 1] << 32) | c[2 * j]);
+                for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
+#pragma unroll
+                for (int h = 0; h < HW; ++h) {
+                    const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
+                    const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
+                    E[h] = gl == 0 ? INF2 : l;
+                    E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
+                }
+            }
+
+            uint32_t SH[NE - 1];
+#pragma unroll
+            for (int j = 0; j < NE - 1; ++j) SH[j] = shift1(E[j], E[j + 1]);
+
+#pragma unroll
+            for (int i = 0; i < KW; ++i) {
+                const int e = HW + i;
+                uint32_t m = __vminu2(E[e], cap);
+                m = __viaddmin_u16x2(SH[e - 1], E1, m);
+                m = __viaddmin_u16x2(SH[e], E1, m);
+                m = __viaddmin_u16x2(E[e - 1], E2, m);
+                m = __viaddmin_u16x2(E[e + 1], E2, m);
+                if (RM >= 4) {
+                    m = __viaddmin_u16x2(SH[e - 2], E3, m);
+                    m = __viaddmin_u16x2(SH[e + 1], E3, m);
+                    m = __viaddmin_u16x2(E[e - 2], E4, m);
+                    m = __viaddmin_u16x2(E[e + 2], E4, m);
+                }
+                uint32_t L = c[i] + m - m2;      // per half: no carry, no borrow
+                if (padded) {
+                    L &= keep[i];
+                    A[i] = L | (INF2 & ~keep[i]);
+                } else {
+                    A[i] = L;
+                }
+                c[i] = L;
+            }
+            if (act) {
+                unsigned long long *sp = (unsigned long long *)(sbase + (int64_t)pix * DWP);
+#pragma unroll
+                for (int j = 0; j < KW / 2; ++j)
+                    atomicAdd(sp + j, ((unsigned long long)c[2 * j + 1] << 32) | c[2 * j]);
+            }
+            prev_lo = cur_lo;
         }
-        prev_lo = cur_lo;
-        x += dx;
-        y += dy;
-        inside = inside && x >= 0 && x < W && y >= 0 && y < H;
     }
 }
 
-template <int KW, int R>
+template <int KW, int RM, bool WIN>
 void launch_stencil(const LevelArgs &a, cudaStream_t s)
 {
     const int maxp = a.W + a.H - 1;
     const int per_block = kStencilWarps * kPathsPerWarp;
     dim3 grid((maxp + per_block - 1) / per_block, a.npaths, a.nviews);
-    agg_stencil<KW, R><<<grid, kStencilWarps * 32, 0, s>>>(a);
+    agg_stencil<KW, RM, WIN><<<grid, kStencilWarps * 32, 0, s>>>(a);
 }
 
 template <int KW>
-void launch_stencil_r(const LevelArgs &a, cudaStream_t s)
+void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
 {
-    switch (a.radius) {
-    case 0: launch_stencil<KW, 0>(a, s); break;
-    case 1: launch_stencil<KW, 1>(a, s); break;
-    case 2: launch_stencil<KW, 2>(a, s); break;
-    case 3: launch_stencil<KW, 3>(a, s); break;
-    default: launch_stencil<KW, 4>(a, s); break;
+    const bool win = a.v[0].lo != nullptr;
+    if (a.radius <= 2) {
+        if (win) launch_stencil<KW, 2, true>(a, s);
+        else launch_stencil<KW, 2, false>(a, s);
+    } else {
+        if (win) launch_stencil<KW, 4, true>(a, s);
+        else launch_stencil<KW, 4, false>(a, s);
     }
 }
 
@@ -405,10 +470,10 @@ void launch_aggregate(const LevelArgs &a, cudaStream_t s)
 {
     if (a.radius <= 4 && a.Dws <= 64) {
         switch (a.Dws / 8) {
-        case 2: launch_stencil_r<2>(a, s); return;
-        case 4: launch_stencil_r<4>(a, s); return;
-        case 6: launch_stencil_r<6>(a, s); return;
-        default: launch_stencil_r<8>(a, s); return;
+        case 2: launch_stencil_kw<2>(a, s); return;
+        case 4: launch_stencil_kw<4>(a, s); return;
+        case 6: launch_stencil_kw<6>(a, s); return;
+        default: launch_stencil_kw<8>(a, s); return;
         }
     }
     const int K = (a.Dw + 31) / 32;

@@ -9,38 +9,49 @@
 // (c1, c2 = C1, C2 scaled by n^2 and rounded) and the cost is
 //     floor(255 (B1 B2 - A1 A2) / (2 B1 B2))  in [0, 255];  255 when x - u < 0.
 //
-// GPU design: one block per (row, 32-pixel tile, view).  The block stages the N rows
-// of I0 and the span of I1 the tile can reach in shared memory, forms per-pixel patch
-// statistics of both images once, and the per-(column, disparity) vertical products
-// Sum_dy I0*I1 once per tile; each node then sums N of those products.  The quotient
-// is estimated in fp32 and made exact with an int64 check only when the estimate
-// lies within 1e-3 of an integer (the fp32 error is below 2e-4; see below).
+// GPU design ("fast SSIM", Fig. fast_ssim, read as running box sums).  One block per
+// 256-pixel row segment and view:
+//  * the block stages, in shared memory, every image column its pixels can reach as the
+//    N patch-row bytes packed in a 64-bit word, and the patch statistics of every centre
+//    (sum S, V = n * sum of squares - S^2, and both as floats);
+//  * each lane owns one label and slides along the row: the cross sum Sxy of pixel x
+//    follows from pixel x-1 by adding the entering column product (two dp4a) and
+//    subtracting the leaving one, kept in a register ring of the last N products; where
+//    the window start changes between neighbours the lane re-sums the N products;
+//  * the quotient is estimated in fp32 from A2 (exact int) and the float statistics and
+//    made exact with an int64 check only when the estimate lies within 1e-3 of an
+//    integer (the estimate's error is below 2e-4; see ssim_quotient).
 #include "mpv_internal.cuh"
 
 namespace mpv {
 
 namespace {
 
-constexpr int TX = 32;       // pixels per tile
-constexpr int UCAP = 256;    // widest disparity span handled with shared column products
-constexpr int kThreads = 256;
+constexpr int kSegPix = 256;          // pixels per block (one row segment)
+constexpr int kCostThreads = 256;
+constexpr int kCostWarps = kCostThreads / 32;
 
-// Floor of 255 (den - num) / (2 den) for |num| <= den, den > 0, exactly.
-// fp32 estimate: A1, A2, B1, B2 are integers below 2^27 in magnitude, so each
-// conversion and product carries relative error <= 2^-24, the quotient <= 2 ulp; the
-// estimate t = 127.5 (1 - num/den) is off by less than 127.5 * 8 * 2^-24 + 3 ulp(255)
-// < 2e-4.  A fractional part in [1e-3, 1 - 1e-3] therefore already has the right floor.
-__device__ __forceinline__ int ssim_quotient(int A1, int A2, int B1, int B2)
+// Floor of 255 (den - num) / (2 den) for |num| <= den, den > 0, exactly, where
+// num = A1 A2 and den = B1 B2.  fA1, fB1, fB2 are float evaluations of A1, B1, B2 (each
+// from at most three correctly rounded operations on exact integers below 2^27: relative
+// error <= 3 * 2^-24), fA2 = (float)A2; the products and the fast division add 4 * 2^-24,
+// so |num/den| <= 1 is known to 10 * 2^-24 and t = 127.5 (1 - num/den) to better than
+// 127.5 * 10 * 2^-24 + 2 ulp(255) < 1.1e-4.  A fractional part of t in [1e-3, 1 - 1e-3]
+// therefore already has the exact floor; otherwise the integers decide.
+__device__ __forceinline__ int ssim_quotient(float fA1, float fA2, float fB1, float fB2,
+                                             int A2, int sx, int vx, int sy, int vy, int c1,
+                                             int c2)
 {
-    const float num = (float)A1 * (float)A2;
-    const float den = (float)B1 * (float)B2;
-    const float t = 127.5f - 127.5f * __fdividef(num, den);
+    const float t = fmaf(-127.5f, __fdividef(fA1 * fA2, fB1 * fB2), 127.5f);
     const float fl = floorf(t);
     const float fr = t - fl;
     int q = (int)fl;
     if (fr < 1e-3f || fr > 1.0f - 1e-3f) {
-        const long long dd = (long long)B1 * (long long)B2;
-        const long long nn = (long long)A1 * (long long)A2;
+        const long long A1 = 2LL * sx * sy + c1;
+        const long long B1 = (long long)sx * sx + (long long)sy * sy + c1;
+        const long long B2 = (long long)vx + vy + c2;
+        const long long dd = B1 * B2;
+        const long long nn = A1 * A2;
         const long long X = 255LL * (dd - nn);
         const long long Y = 2LL * dd;
         q = min(max(q, 0), 255);
@@ -57,176 +68,228 @@ __device__ __forceinline__ int ssim_quotient(int A1, int A2, int B1, int B2)
     return q;
 }
 
+// Shared-memory layout of one block.
+struct CostSmem {
+    int ncol0, ncol1;     // staged columns of I0 and I1
+    int nc1;              // I1 centres with statistics
+    size_t off_col0, off_col1, off_cs, off_st0, off_st1, bytes;
+};
+
+__host__ __device__ inline CostSmem cost_smem_layout(int R, int uspan_max)
+{
+    CostSmem L;
+    L.ncol0 = kSegPix + 2 * R + 2;
+    L.ncol1 = kSegPix + 2 * R + 1 + uspan_max;
+    L.nc1 = kSegPix + uspan_max;
+    size_t o = 0;
+    L.off_col0 = o;
+    o += sizeof(uint2) * L.ncol0;
+    L.off_col1 = o;
+    o += sizeof(uint2) * L.ncol1;
+    L.off_cs = o;                          // column sums and sums of squares (int2)
+    o += sizeof(int2) * (L.ncol1 > L.ncol0 ? L.ncol1 : L.ncol0);
+    o = (o + 15) & ~(size_t)15;
+    L.off_st0 = o;                         // I0 statistics of the segment's pixels
+    o += sizeof(int4) * kSegPix;
+    L.off_st1 = o;                         // I1 statistics of the reachable centres
+    o += sizeof(int4) * L.nc1;
+    L.bytes = o;
+    return L;
+}
+
 template <int N>
-__global__ void __launch_bounds__(kThreads) cost_kernel(LevelArgs a)
+__device__ __forceinline__ int colprod(uint2 a, uint2 b)
+{
+    return (int)__dp4a(a.x, b.x, N == 5 ? __dp4a(a.y, b.y, 0u) : 0u);
+}
+
+// Packs column xc (clamped) of rows y-R..y+R (clamped) and returns (sum, sum of squares).
+template <int N>
+__device__ __forceinline__ uint2 pack_column(const uint8_t *img, int pitch, int W, int H, int y,
+                                             int xc, int2 &ss)
+{
+    constexpr int R = N / 2;
+    const int xa = min(max(xc, 0), W - 1);
+    uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        const int yy = min(max(y - R + r, 0), H - 1);
+        const uint32_t v = img[(int64_t)yy * pitch + xa];
+        if (r < 4)
+            w0 |= v << (8 * r);
+        else
+            w1 = v;
+    }
+    ss.x = (int)__dp4a(w0, 0x01010101u, w1);
+    ss.y = (int)__dp4a(w0, w0, w1 * w1);
+    return make_uint2(w0, w1);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kCostThreads) cost_kernel(LevelArgs a, int uspan_max)
 {
     constexpr int R = N / 2;
     constexpr int n = N * N;
+    constexpr int NR = 2 * R + 1;          // ring of column products
     const int view = blockIdx.z;
     const ViewLevel &V = a.v[view];
-    const int W = a.W, H = a.H, Dw = a.Dw;
+    const int W = a.W, H = a.H, Dw = a.Dw, Dws = a.Dws;
     const int y = blockIdx.y;
-    const int x0 = blockIdx.x * TX;
-    const int nx = min(TX, W - x0);
+    const int x0 = blockIdx.x * kSegPix;
+    const int npx = min(kSegPix, W - x0);
     const int tid = threadIdx.x;
+    const int c1 = a.c1, c2 = a.c2;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int lo_s[TX];
-    __shared__ int sx_s[TX], sxq_s[TX], vx_s[TX];
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int lo_s[kSegPix];
     __shared__ int red[2];
-    __shared__ uint8_t i0_s[N][TX + 2 * R];
+    const CostSmem L = cost_smem_layout(R, uspan_max);
+    uint2 *col0 = (uint2 *)(smem + L.off_col0);
+    uint2 *col1 = (uint2 *)(smem + L.off_col1);
+    int2 *cs = (int2 *)(smem + L.off_cs);
+    int4 *st0 = (int4 *)(smem + L.off_st0);
+    int4 *st1 = (int4 *)(smem + L.off_st1);
 
     if (tid == 0) {
         red[0] = 0x7FFFFFFF;
         red[1] = 0;
     }
     __syncthreads();
-    if (tid < nx) {
-        const int l = V.lo ? (int)V.lo[(int64_t)y * W + x0 + tid] : 0;
-        lo_s[tid] = l;
+    for (int i = tid; i < npx; i += kCostThreads) {
+        const int l = V.lo ? (int)V.lo[(int64_t)y * W + x0 + i] : 0;
+        lo_s[i] = l;
         atomicMin(&red[0], l);
         atomicMax(&red[1], l);
     }
     __syncthreads();
-    const int minlo = red[0], maxlo = red[1];
-    const int U = maxlo - minlo + Dw;                  // disparity span of the tile
-    const int bmin = x0 - R - (maxlo + Dw - 1);         // first I1 column reached
-    const int WB = nx + 2 * R + U - 1;                  // I1 columns staged
-    const int NC = WB - 2 * R;                          // I1 patch centres
-    const bool use_cp = U <= UCAP;
-    const int CPW = TX + 2 * R + 1;                     // odd row stride: no bank conflicts
+    const int umin = red[0], umax = red[1] + Dw - 1;
+    const int uspan = umax - umin;
+    const int b0 = x0 - R - 1 - umax;       // first staged I1 column
+    const int a0 = x0 - R - 1;              // first staged I0 column
+    const int nb = npx + 2 * R + 1 + uspan; // staged I1 columns
+    const int na = npx + 2 * R + 2;
+    const int ncen = npx + uspan;           // I1 centres x0 - umax .. x0 + npx - 1 - umin
 
-    uint8_t *i1_s = smem_raw;                                     // [N][WB]
-    int *sy_s = (int *)(smem_raw + ((N * WB + 15) & ~15));        // [NC]
-    int *syq_s = sy_s + NC;                                       // [NC]
-    int *vy_s = syq_s + NC;                                       // [NC]
-    int *cp_s = vy_s + NC;                                        // [U][CPW]
-
-    // stage rows y-R..y+R of I0 (tile + halo) and of I1 (reachable span), clamped
-    for (int i = tid; i < N * (TX + 2 * R); i += kThreads) {
-        const int dy = i / (TX + 2 * R), c = i % (TX + 2 * R);
-        const int yy = min(max(y + dy - R, 0), H - 1);
-        const int xx = min(max(x0 - R + c, 0), W - 1);
-        i0_s[dy][c] = V.I0[(int64_t)yy * V.pitch0 + xx];
-    }
-    for (int i = tid; i < N * WB; i += kThreads) {
-        const int dy = i / WB, c = i % WB;
-        const int yy = min(max(y + dy - R, 0), H - 1);
-        const int xx = min(max(bmin + c, 0), W - 1);
-        i1_s[i] = V.I1[(int64_t)yy * V.pitch1 + xx];
+    // I0: packed columns, column sums, then patch statistics of the segment's pixels
+    for (int i = tid; i < na; i += kCostThreads) {
+        int2 ss;
+        col0[i] = pack_column<N>(V.I0, V.pitch0, W, H, y, a0 + i, ss);
+        cs[i] = ss;
     }
     __syncthreads();
-
-    // patch statistics: I0 for the tile's pixels, I1 for every reachable centre
-    if (tid < nx) {
+    for (int i = tid; i < npx; i += kCostThreads) {
         int s = 0, q = 0;
 #pragma unroll
-        for (int dy = 0; dy < N; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < N; ++dx) {
-                const int v = i0_s[dy][tid + dx];
-                s += v;
-                q += v * v;
-            }
-        sx_s[tid] = s;
-        sxq_s[tid] = s * s;
-        vx_s[tid] = n * q - s * s;
-    }
-    for (int c = tid; c < NC; c += kThreads) {
-        int s = 0, q = 0;
-#pragma unroll
-        for (int dy = 0; dy < N; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < N; ++dx) {
-                const int v = i1_s[dy * WB + c + dx];
-                s += v;
-                q += v * v;
-            }
-        sy_s[c] = s;
-        syq_s[c] = s * s;
-        vy_s[c] = n * q - s * s;
-    }
-    // vertical products P(a, uu) = sum_dy I0(y+dy, a) * I1(y+dy, a - minlo - uu)
-    if (use_cp) {
-        const int na = nx + 2 * R;
-        for (int i = tid; i < U * na; i += kThreads) {
-            const int uu = i / na, col = i % na;
-            const int b = col + (U - 1) - uu;           // I1 staged column of a - u
-            int acc = 0;
-#pragma unroll
-            for (int dy = 0; dy < N; ++dy) acc += (int)i0_s[dy][col] * (int)i1_s[dy * WB + b];
-            cp_s[uu * CPW + col] = acc;
+        for (int d = 0; d < NR; ++d) {   // centre x0+i is staged column i + R + 1
+            const int2 t = cs[i + 1 + d];
+            s += t.x;
+            q += t.y;
         }
+        const int v = n * q - s * s;
+        st0[i] = make_int4(s, v, __float_as_int((float)s), __float_as_int((float)v));
+    }
+    __syncthreads();
+    // I1: packed columns, column sums, statistics of every reachable centre
+    for (int i = tid; i < nb; i += kCostThreads) {
+        int2 ss;
+        col1[i] = pack_column<N>(V.I1, V.pitch1, W, H, y, b0 + i, ss);
+        cs[i] = ss;
+    }
+    __syncthreads();
+    for (int i = tid; i < ncen; i += kCostThreads) {
+        // centre x' = x0 - umax + i is staged column i + R + 1
+        int s = 0, q = 0;
+#pragma unroll
+        for (int d = 0; d < NR; ++d) {
+            const int2 t = cs[i + 1 + d];
+            s += t.x;
+            q += t.y;
+        }
+        const int v = n * q - s * s;
+        st1[i] = make_int4(s, v, __float_as_int((float)s), __float_as_int((float)v));
     }
     __syncthreads();
 
-    const int c1 = a.c1, c2 = a.c2;
-    const int Dws = a.Dws;
     const int lane = tid & 31, warp = tid >> 5;
-    // one warp per pixel, lanes over labels: the pixel's Dws cost bytes are contiguous
-    for (int i = warp; i < nx; i += kThreads / 32) {
-        uint8_t *out = V.C + ((int64_t)y * W + x0 + i) * Dws;
-        const int lo = lo_s[i];
-        const int sx = sx_s[i], sxq = sxq_s[i], vx = vx_s[i];
-        for (int k = lane; k < Dws; k += 32) {
-            const int u = lo + k;
-            const int xp = x0 + i - u;
-            int q = 255;
-            if (k < Dw && xp >= 0) {
-                int sxy = 0;
-                if (use_cp) {
-                    const int *row = cp_s + (lo - minlo + k) * CPW + i;
+    const int LP = Dws < 32 ? Dws : 32;     // lanes per pixel stream
+    const int nsub = 32 / LP;
+    const int sub = lane / LP, kl = lane - sub * LP;
+    const int per_warp = kSegPix / kCostWarps;
+    const int sub_len = per_warp / nsub;
+    const int xs = warp * per_warp + sub * sub_len;      // segment-relative
+    const int xe = min(xs + sub_len, npx);
+    const float c1f = (float)c1, c2f = (float)c2;
+    uint8_t *out = V.C + ((int64_t)y * W + x0) * Dws;
+
+    for (int k = kl; k < Dws; k += LP) {
+        if (k >= Dw) {           // padding labels: never read as costs
+            for (int x = xs; x < xe; ++x) out[(int64_t)x * Dws + k] = 255;
+            continue;
+        }
+        int ring[NR];
+        int sxy = 0;
+        int prev_lo = -1;
+        for (int xb = xs; xb < xe; xb += NR) {
 #pragma unroll
-                    for (int dx = 0; dx < N; ++dx) sxy += row[dx];
-                } else {
-                    const int b0 = xp - R - bmin;
+            for (int j = 0; j < NR; ++j) {
+                const int x = xb + j;            // segment-relative pixel
+                if (x < xe) {
+                    const int lo = lo_s[x];
+                    const int u = lo + k;
+                    // I0 column of virtual column x0+x+d is staged at x + 1 + R + d;
+                    // I1 column of x0+x+d-u at x + 1 + R + d + umax - u
+                    const int ib = x + 1 + R + umax - u;
+                    if (lo != prev_lo) {
+                        sxy = 0;
 #pragma unroll
-                    for (int dy = 0; dy < N; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < N; ++dx)
-                            sxy += (int)i0_s[dy][i + dx] * (int)i1_s[dy * WB + b0 + dx];
+                        for (int d = -R; d <= R; ++d) {
+                            const int p = colprod<N>(col0[x + 1 + R + d], col1[ib + d]);
+                            ring[(j + d + NR) % NR] = p;
+                            sxy += p;
+                        }
+                        prev_lo = lo;
+                    } else {
+                        const int p = colprod<N>(col0[x + 1 + 2 * R], col1[ib + R]);
+                        sxy += p - ring[(j + R) % NR];
+                        ring[(j + R) % NR] = p;
+                    }
+                    const int xp = x0 + x - u;
+                    int q = 255;
+                    if (xp >= 0) {
+                        const int4 s0 = st0[x];
+                        const int4 s1 = st1[x + umax - u];
+                        const int A2 = 2 * (n * sxy - s0.x * s1.x) + c2;
+                        const float fsx = __int_as_float(s0.z), fsy = __int_as_float(s1.z);
+                        const float fA1 = fmaf(2.0f * fsx, fsy, c1f);
+                        const float fB1 = fmaf(fsx, fsx, fmaf(fsy, fsy, c1f));
+                        const float fB2 = __int_as_float(s0.w) + (__int_as_float(s1.w) + c2f);
+                        q = ssim_quotient(fA1, (float)A2, fB1, fB2, A2, s0.x, s0.y, s1.x, s1.y,
+                                          c1, c2);
+                    }
+                    out[(int64_t)x * Dws + k] = (uint8_t)q;
                 }
-                const int cc = xp - R - bmin;           // I1 centre index
-                const int sy = sy_s[cc];
-                const int sxsy = sx * sy;
-                const int A1 = 2 * sxsy + c1;
-                const int B1 = sxq + syq_s[cc] + c1;
-                const int A2 = 2 * (n * sxy - sxsy) + c2;
-                const int B2 = vx + vy_s[cc] + c2;
-                q = ssim_quotient(A1, A2, B1, B2);
             }
-            out[k] = (uint8_t)q;
         }
     }
-}
-
-size_t cost_smem_bytes(int N, int Dmax, int Dw)
-{
-    const int R = N / 2;
-    const int U = Dmax;   // upper bound of the span (maxlo - minlo + Dw <= D)
-    const int WB = TX + 2 * R + U - 1;
-    const int NC = WB - 2 * R;
-    size_t b = (size_t)((N * WB + 15) & ~15) + 3 * sizeof(int) * (size_t)NC;
-    const int ucp = U < UCAP ? U : UCAP;
-    b += sizeof(int) * (size_t)ucp * (TX + 2 * R + 1);
-    (void)Dw;
-    return b;
 }
 
 }  // namespace
 
 void launch_cost(const LevelArgs &a, cudaStream_t s)
 {
-    dim3 grid((a.W + TX - 1) / TX, a.H, a.nviews);
-    const size_t smem = cost_smem_bytes(a.N, a.D, a.Dw);
+    // widest disparity span of a segment: window starts lie in [0, D - Dw]
+    const int uspan_max = a.D - 1;
+    const int R = a.N / 2;
+    const CostSmem L = cost_smem_layout(R, uspan_max);
+    dim3 grid((a.W + kSegPix - 1) / kSegPix, a.H, a.nviews);
     if (a.N == 5) {
         cudaFuncSetAttribute(cost_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cost_kernel<5><<<grid, kThreads, smem, s>>>(a);
+                             (int)L.bytes);
+        cost_kernel<5><<<grid, kCostThreads, L.bytes, s>>>(a, uspan_max);
     } else {
         cudaFuncSetAttribute(cost_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cost_kernel<3><<<grid, kThreads, smem, s>>>(a);
+                             (int)L.bytes);
+        cost_kernel<3><<<grid, kCostThreads, L.bytes, s>>>(a, uspan_max);
     }
 }
 
