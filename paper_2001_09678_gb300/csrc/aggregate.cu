@@ -64,9 +64,10 @@ __device__ __forceinline__ void path_start(int dx, int dy, int W, int H, int i, 
 // agg_stencil
 // ---------------------------------------------------------------------------------
 
-constexpr int kG = 4;                       // lanes per scan path
 constexpr int kStencilWarps = 4;            // warps per block
-constexpr int kPathsPerWarp = 32 / kG;
+// lanes per scan path for 32- and 64-label strides (4 labels, resp. 8, per lane): more
+// independent warps per SM hide the per-step dependency latency better than 4 lanes
+constexpr int kLanesWide = 8;
 
 // Prefetch loads of the scan paths.  Written as volatile asm so that the compiler keeps
 // them where they are issued (PF steps ahead of their use) instead of re-issuing a
@@ -109,9 +110,11 @@ __device__ __forceinline__ int path_length(int dx, int dy, int W, int H, int x0,
 // RM (ceil(T/p1) - 1 <= RM) the stencil min over |d| <= RM plus the cap min_v A(v) + T
 // is the full-connectivity minimum.  WIN: the level has per-pixel windows, and the
 // predecessor is re-indexed into the current window through shared memory every step.
-template <int KW, int RM, bool WIN>
+template <int G, int KW, int RM, bool WIN>
 __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
 {
+    constexpr int kG = G;                    // lanes per scan path
+    constexpr int kPathsPerWarp = 32 / kG;
     constexpr int HW = RM / 2;               // halo words per side
     constexpr int NE = KW + 2 * HW;          // words with halos
     constexpr int K = 2 * KW;                // labels per lane
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
     const int dx = c_dirs[dir][0], dy = c_dirs[dir][1];
     const int W = a.W, H = a.H, Dw = a.Dw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gl = lane & (kG - 1), grp = lane >> 2;
+    const int gl = lane & (kG - 1), grp = lane / kG;
     const int path = (blockIdx.x * kStencilWarps + warp) * kPathsPerWarp + grp;
     const ViewLevel &V = a.v[view];
 
@@ -214,8 +217,8 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
 #pragma unroll
             for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
             m2 = __vminu2(m2, __byte_perm(m2, m2, 0x1032));
-            m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, 1));
-            m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, 2));
+#pragma unroll
+            for (int o = 1; o < kG; o <<= 1) m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, o));
             const uint32_t cap = m2 + Tx2;
 
             // predecessor words around this lane's labels, HW halo words per side
@@ -276,35 +279,41 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
                 c[i] = L;
             }
             if (act) {
-                unsigned long long *sp = (unsigned long long *)(sbase + (int64_t)pix * DWP);
+                if (KW % 2 == 0) {
+                    unsigned long long *sp = (unsigned long long *)(sbase + (int64_t)pix * DWP);
 #pragma unroll
-                for (int j = 0; j < KW / 2; ++j)
-                    atomicAdd(sp + j, ((unsigned long long)c[2 * j + 1] << 32) | c[2 * j]);
+                    for (int j = 0; j < KW / 2; ++j)
+                        atomicAdd(sp + j, ((unsigned long long)c[2 * j + 1] << 32) | c[2 * j]);
+                } else {
+                    unsigned int *sp = (unsigned int *)(sbase + (int64_t)pix * DWP);
+#pragma unroll
+                    for (int j = 0; j < KW; ++j) atomicAdd(sp + j, c[j]);
+                }
             }
             prev_lo = cur_lo;
         }
     }
 }
 
-template <int KW, int RM, bool WIN>
+template <int G, int KW, int RM, bool WIN>
 void launch_stencil(const LevelArgs &a, cudaStream_t s)
 {
     const int maxp = a.W + a.H - 1;
-    const int per_block = kStencilWarps * kPathsPerWarp;
+    const int per_block = kStencilWarps * (32 / G);
     dim3 grid((maxp + per_block - 1) / per_block, a.npaths, a.nviews);
-    agg_stencil<KW, RM, WIN><<<grid, kStencilWarps * 32, 0, s>>>(a);
+    agg_stencil<G, KW, RM, WIN><<<grid, kStencilWarps * 32, 0, s>>>(a);
 }
 
-template <int KW>
+template <int G, int KW>
 void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
 {
     const bool win = a.v[0].lo != nullptr;
     if (a.radius <= 2) {
-        if (win) launch_stencil<KW, 2, true>(a, s);
-        else launch_stencil<KW, 2, false>(a, s);
+        if (win) launch_stencil<G, KW, 2, true>(a, s);
+        else launch_stencil<G, KW, 2, false>(a, s);
     } else {
-        if (win) launch_stencil<KW, 4, true>(a, s);
-        else launch_stencil<KW, 4, false>(a, s);
+        if (win) launch_stencil<G, KW, 4, true>(a, s);
+        else launch_stencil<G, KW, 4, false>(a, s);
     }
 }
 
@@ -469,11 +478,11 @@ void launch_scan(const LevelArgs &a, cudaStream_t s)
 void launch_aggregate(const LevelArgs &a, cudaStream_t s)
 {
     if (a.radius <= 4 && a.Dws <= 64) {
-        switch (a.Dws / 8) {
-        case 2: launch_stencil_kw<2>(a, s); return;
-        case 4: launch_stencil_kw<4>(a, s); return;
-        case 6: launch_stencil_kw<6>(a, s); return;
-        default: launch_stencil_kw<8>(a, s); return;
+        switch (a.Dws) {
+        case 16: launch_stencil_kw<4, 2>(a, s); return;
+        case 32: launch_stencil_kw<kLanesWide, 32 / (2 * kLanesWide)>(a, s); return;
+        case 48: launch_stencil_kw<4, 6>(a, s); return;
+        default: launch_stencil_kw<kLanesWide, 64 / (2 * kLanesWide)>(a, s); return;
         }
     }
     const int K = (a.Dw + 31) / 32;
