@@ -223,12 +223,23 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
 
             // predecessor words around this lane's labels, HW halo words per side
             uint32_t E[NE];
-            if (WIN) {
+#pragma unroll
+            for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
+#pragma unroll
+            for (int h = 0; h < HW; ++h) {
+                const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
+                const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
+                E[h] = gl == 0 ? INF2 : l;
+                E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
+            }
+            // a path whose window moved re-indexes its predecessor through shared memory
+            // (the whole warp does, when any of its paths moved)
+            const int s = (WIN && act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
+            if (WIN && __any_sync(kFull, s != 0)) {
                 uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
 #pragma unroll
                 for (int i = 0; i < KW; ++i) gw[i] = A[i];
                 __syncwarp();
-                const int s = (act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
                 const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
                 const int j0 = PAD + gl * K - 2 * HW + sc;
                 const uint32_t *gwords = (const uint32_t *)gb + (j0 >> 1);
@@ -239,16 +250,6 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
 #pragma unroll
                 for (int w = 0; w < NE; ++w) E[w] = __byte_perm(Wd[w], Wd[w + 1], sel);
                 __syncwarp();
-            } else {
-#pragma unroll
-                for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
-#pragma unroll
-                for (int h = 0; h < HW; ++h) {
-                    const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
-                    const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
-                    E[h] = gl == 0 ? INF2 : l;
-                    E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
-                }
             }
 
             uint32_t SH[NE - 1];
