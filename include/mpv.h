@@ -118,9 +118,20 @@ mpv_status mpv_match_host(mpv_ctx *ctx, const uint8_t *left, const uint8_t *righ
                           int32_t disp_pitch, void *cuda_stream);
 
 /* Matches n pairs of possibly different sizes and ranges in one submission.  Each pair
- * is validated first; if any is invalid nothing is launched.  The batch is replayed
- * from a CUDA graph when the same batch signature (sizes, ranges, pointers) repeats. */
+ * is validated first; if any is invalid nothing is launched.  For n > 1 the whole batch
+ * is captured once as a CUDA graph in which the pairs run concurrently on the context's
+ * worker streams (largest first), each with the launch shapes the autotuner chose for
+ * its image shape (tuning an unseen shape runs its pair a few extra times first); the
+ * graph is cached by the batch signature (sizes, ranges, pointers, parameters) and a
+ * repeated batch costs one graph launch on `cuda_stream`.  Outputs are identical to
+ * matching each pair alone.  Do not call it while `cuda_stream` is being captured.    */
 mpv_status mpv_match_batch(mpv_ctx *ctx, const mpv_pair *pairs, int32_t n, void *cuda_stream);
+
+/* Autotuner: times the candidate launch shapes of the matcher on `pair` (its buffers are
+ * used and overwritten) and keeps the fastest for pairs of the same width, height and
+ * range; *lanes (may be NULL) receives the chosen lanes per scan path of the
+ * aggregation (4 or 8).  Synchronous.  Results do not depend on the choice.          */
+mpv_status mpv_autotune(mpv_ctx *ctx, const mpv_pair *pair, int32_t *lanes);
 
 /* Loads the learned-proposal network weights (used when proposal = LEARNED). */
 mpv_status mpv_load_proposal_weights(mpv_ctx *ctx, const char *path);

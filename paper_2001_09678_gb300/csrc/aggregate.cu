@@ -65,8 +65,9 @@ __device__ __forceinline__ void path_start(int dx, int dy, int W, int H, int i, 
 // ---------------------------------------------------------------------------------
 
 constexpr int kStencilWarps = 4;            // warps per block
-// lanes per scan path for 32- and 64-label strides (4 labels, resp. 8, per lane): more
-// independent warps per SM hide the per-step dependency latency better than 4 lanes
+// lanes per scan path for 32- and 64-label strides when the tuning asks for the wide
+// form (4 labels, resp. 8, per lane): more independent warps per SM hide the per-step
+// dependency latency better than 4 lanes on large levels
 constexpr int kLanesWide = 8;
 
 // Prefetch loads of the scan paths.  Written as volatile asm so that the compiler keeps
@@ -479,11 +480,18 @@ void launch_scan(const LevelArgs &a, cudaStream_t s)
 void launch_aggregate(const LevelArgs &a, cudaStream_t s)
 {
     if (a.radius <= 4 && a.Dws <= 64) {
+        const bool wide = a.lanes == kLanesWide;
         switch (a.Dws) {
         case 16: launch_stencil_kw<4, 2>(a, s); return;
-        case 32: launch_stencil_kw<kLanesWide, 32 / (2 * kLanesWide)>(a, s); return;
+        case 32:
+            if (wide) launch_stencil_kw<kLanesWide, 32 / (2 * kLanesWide)>(a, s);
+            else launch_stencil_kw<4, 4>(a, s);
+            return;
         case 48: launch_stencil_kw<4, 6>(a, s); return;
-        default: launch_stencil_kw<kLanesWide, 64 / (2 * kLanesWide)>(a, s); return;
+        default:
+            if (wide) launch_stencil_kw<kLanesWide, 64 / (2 * kLanesWide)>(a, s);
+            else launch_stencil_kw<4, 8>(a, s);
+            return;
         }
     }
     const int K = (a.Dw + 31) / 32;

@@ -1,7 +1,9 @@
 // mpv_api.cu -- C ABI of the matcher: contexts, validation, workspace, launch sequence.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -28,6 +30,20 @@ struct mpv_ctx {
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
     int64_t launches[MPV_NUM_STAGES] = {};
+    // batches: worker streams, capture stream, fork/join events, per-worker workspaces,
+    // instantiated graphs keyed by batch signature, autotuned launch shapes per shape
+    std::vector<cudaStream_t> workers;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    void *bws = nullptr;
+    size_t bws_bytes = 0;
+    struct Graph {
+        uint64_t sig;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    std::map<uint64_t, Tuning> tuning;
 };
 
 namespace {
@@ -90,6 +106,215 @@ void hook_end(void *user, int stage, cudaStream_t s)
     cudaEventRecord(ctx->recs.back().b, s);
 }
 
+
+constexpr int kBatchStreams = 16;
+constexpr size_t kMaxGraphs = 8;
+
+uint64_t mix64(uint64_t h, uint64_t v)
+{
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h * 0xFF51AFD7ED558CCDull;
+}
+
+uint64_t shape_key(const mpv_params &p, int W, int H, int D)
+{
+    uint64_t h = mix64(0, (uint64_t)W);
+    h = mix64(h, (uint64_t)H);
+    h = mix64(h, (uint64_t)D);
+    const uint32_t *w = (const uint32_t *)&p;
+    for (size_t i = 0; i < sizeof(mpv_params) / 4; ++i) h = mix64(h, w[i]);
+    return h;
+}
+
+mpv_status ensure_batch_streams(mpv_ctx *ctx)
+{
+    if (!ctx->workers.empty()) return MPV_OK;
+    if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return MPV_ERR_CUDA;
+    }
+    for (int i = 0; i < kBatchStreams; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return MPV_ERR_CUDA;
+        }
+        ctx->workers.push_back(s);
+        ctx->joins.push_back(e);
+    }
+    return MPV_OK;
+}
+
+void drop_graphs(mpv_ctx *ctx)
+{
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
+// Autotuner: times the whole matcher on `job` once per candidate launch shape (after a
+// warm-up run) on the context's workspace, and keeps the fastest.  Every candidate gives
+// the same bit-exact result; only the time differs.
+mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
+{
+    const uint64_t key = shape_key(ctx->p, job.W, job.H, job.D);
+    auto it = ctx->tuning.find(key);
+    if (it != ctx->tuning.end()) {
+        out = it->second;
+        return MPV_OK;
+    }
+    mpv_status st = ensure_batch_streams(ctx);
+    if (st != MPV_OK) return st;
+    // earlier calls may still use the context workspace on the caller's stream
+    cudaStreamSynchronize(ctx->last_stream);
+    Geometry g;
+    make_geometry(ctx->p, job.W, job.H, job.D, g);
+    st = ensure_workspace(ctx, make_layout(g, views_needed(ctx->p, job, nullptr)).total);
+    if (st != MPV_OK) return st;
+    cudaStream_t s = ctx->workers[0];
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cands[2] = {8, 4};
+    float best = 1e30f;
+    Tuning bt;
+    for (int c : cands) {
+        Tuning t;
+        t.lanes = c;
+        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t);
+        float tot = 0.f;
+        for (int r = 0; r < 2; ++r) {
+            cudaEventRecord(e0, s);
+            enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            bt = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    ctx->tuning[key] = bt;
+    out = bt;
+    return MPV_OK;
+}
+
+// Runs a batch as one CUDA graph: pair i runs on worker stream w(i) (largest pairs
+// first, round robin), pairs sharing a worker run one after another and share that
+// worker's workspace region, and the workers run concurrently.  The instantiated graph
+// is cached by the batch signature and replayed by a single graph launch.
+mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stream)
+{
+    mpv_status st = ensure_batch_streams(ctx);
+    if (st != MPV_OK) return st;
+    std::vector<Tuning> tune(n);
+    for (int i = 0; i < n; ++i) {
+        st = autotune(ctx, jobs[i], tune[i]);
+        if (st != MPV_OK) return st;
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (int64_t)jobs[a].W * jobs[a].H * jobs[a].D > (int64_t)jobs[b].W * jobs[b].H * jobs[b].D;
+    });
+    const int nw = std::min(n, kBatchStreams);
+    std::vector<int> worker(n);
+    std::vector<size_t> wbytes(nw, 0), woff(nw, 0);
+    for (int r = 0; r < n; ++r) {
+        const int i = order[r];
+        worker[i] = r % nw;
+        Geometry g;
+        make_geometry(ctx->p, jobs[i].W, jobs[i].H, jobs[i].D, g);
+        const size_t b = make_layout(g, views_needed(ctx->p, jobs[i], nullptr)).total;
+        wbytes[worker[i]] = std::max(wbytes[worker[i]], b);
+    }
+    size_t total = 0;
+    for (int w = 0; w < nw; ++w) {
+        woff[w] = total;
+        total += (wbytes[w] + 255) & ~(size_t)255;
+    }
+    if (total > ctx->bws_bytes) {
+        if (ctx->ws_limit && total > ctx->ws_limit) return MPV_ERR_OOM;
+        drop_graphs(ctx);
+        if (ctx->bws) {
+            cudaDeviceSynchronize();
+            cudaFree(ctx->bws);
+            ctx->bws = nullptr;
+            ctx->bws_bytes = 0;
+        }
+        const cudaError_t e = cudaMalloc(&ctx->bws, total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+        ctx->bws_bytes = total;
+    }
+    uint64_t sig = mix64(shape_key(ctx->p, n, nw, 0), (uint64_t)(uintptr_t)ctx->bws);
+    for (int i = 0; i < n; ++i) {
+        const PairJob &j = jobs[i];
+        sig = mix64(sig, (uint64_t)(uintptr_t)j.left);
+        sig = mix64(sig, (uint64_t)(uintptr_t)j.right);
+        sig = mix64(sig, (uint64_t)(uintptr_t)j.disp);
+        sig = mix64(sig, (uint64_t)(uintptr_t)j.disp_right);
+        sig = mix64(sig, ((uint64_t)j.W << 32) | (uint32_t)j.H);
+        sig = mix64(sig, ((uint64_t)j.pitch << 32) | (uint32_t)j.disp_pitch);
+        sig = mix64(sig, ((uint64_t)j.D << 32) | (uint32_t)tune[i].lanes);
+    }
+    for (size_t k = 0; k < ctx->graphs.size(); ++k)
+        if (ctx->graphs[k].sig == sig) {
+            const cudaError_t e = cudaGraphLaunch(ctx->graphs[k].exec, stream);
+            return cuda_status(e);
+        }
+
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MPV_ERR_CUDA;
+    }
+    cudaEventRecord(ctx->fork, ctx->cap);
+    for (int w = 0; w < nw; ++w) cudaStreamWaitEvent(ctx->workers[w], ctx->fork, 0);
+    mpv_status est = MPV_OK;
+    for (int r = 0; r < n && est == MPV_OK; ++r) {
+        const int i = order[r];
+        const int w = worker[i];
+        est = enqueue_pair(ctx->p, jobs[i], (uint8_t *)ctx->bws + woff[w], ctx->workers[w],
+                           nullptr, nullptr, tune[i]);
+    }
+    for (int w = 0; w < nw; ++w) {
+        cudaEventRecord(ctx->joins[w], ctx->workers[w]);
+        cudaStreamWaitEvent(ctx->cap, ctx->joins[w], 0);
+    }
+    e = cudaStreamEndCapture(ctx->cap, &graph);
+    if (e != cudaSuccess || est != MPV_OK) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        return est != MPV_OK ? est : MPV_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MPV_ERR_CUDA;
+    }
+    if (ctx->graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(ctx->graphs.front().exec);
+        ctx->graphs.erase(ctx->graphs.begin());
+    }
+    ctx->graphs.push_back({sig, exec});
+    return cuda_status(cudaGraphLaunch(exec, stream));
+}
+
 // Enqueues one pair with the context's workspace and profiler.
 mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const StageSink *dbg)
 {
@@ -99,7 +324,10 @@ mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const Stage
     const mpv_status st = ensure_workspace(ctx, L.total);
     if (st != MPV_OK) return st;
     StageHook hook{hook_begin, hook_end, ctx};
-    return enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg);
+    Tuning t;
+    const auto it = ctx->tuning.find(shape_key(ctx->p, job.W, job.H, job.D));
+    if (it != ctx->tuning.end()) t = it->second;
+    return enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t);
 }
 
 struct DeviceGuard {
@@ -208,15 +436,32 @@ mpv_status mpv_match_batch(mpv_ctx *ctx, const mpv_pair *pairs, int32_t n, void 
     DeviceGuard guard(ctx->device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     ctx->last_stream = s;
+    std::vector<PairJob> jobs(n);
     for (int i = 0; i < n; ++i) {
         const mpv_pair &q = pairs[i];
-        PairJob j{q.left, q.right, q.width, q.height, q.pitch,
-                  q.max_disparity > 0 ? q.max_disparity : ctx->p.max_disparity,
-                  q.disp, q.disp_pitch, q.disp_right};
-        const mpv_status st = enqueue(ctx, j, s, nullptr);
-        if (st != MPV_OK) return st;
+        jobs[i] = PairJob{q.left, q.right, q.width, q.height, q.pitch,
+                          q.max_disparity > 0 ? q.max_disparity : ctx->p.max_disparity,
+                          q.disp, q.disp_pitch, q.disp_right};
     }
-    return MPV_OK;
+    if (n == 1) return enqueue(ctx, jobs[0], s, nullptr);
+    if (n == 0) return MPV_OK;
+    return run_batch(ctx, jobs.data(), n, s);
+}
+
+mpv_status mpv_autotune(mpv_ctx *ctx, const mpv_pair *pair, int32_t *lanes)
+{
+    if (!ctx || !pair || !pair->left || !pair->right || !pair->disp) return MPV_ERR_INVALID_ARG;
+    const int D = pair->max_disparity > 0 ? pair->max_disparity : ctx->p.max_disparity;
+    const mpv_status v = validate_pair(ctx->p, pair->width, pair->height, pair->pitch,
+                                       pair->disp_pitch, D);
+    if (v != MPV_OK) return v;
+    DeviceGuard guard(ctx->device);
+    const PairJob job{pair->left, pair->right, pair->width, pair->height, pair->pitch, D,
+                      pair->disp, pair->disp_pitch, pair->disp_right};
+    Tuning t;
+    const mpv_status st = autotune(ctx, job, t);
+    if (st == MPV_OK && lanes) *lanes = t.lanes;
+    return st;
 }
 
 mpv_status mpv_match_host(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
@@ -396,6 +641,15 @@ void mpv_destroy(mpv_ctx *ctx)
             cudaEventDestroy(r.b);
         }
         for (auto e : ctx->pool) cudaEventDestroy(e);
+        drop_graphs(ctx);
+        for (auto s : ctx->workers) cudaStreamDestroy(s);
+        for (auto e : ctx->joins) cudaEventDestroy(e);
+        if (ctx->cap) cudaStreamDestroy(ctx->cap);
+        if (ctx->fork) cudaEventDestroy(ctx->fork);
+        if (ctx->bws) {
+            cudaDeviceSynchronize();
+            cudaFree(ctx->bws);
+        }
     }
     if (ctx->ws || ctx->stage) {
         DeviceGuard guard(ctx->device);

@@ -44,6 +44,12 @@ struct LevelArgs {
     int trunc;       // effective truncation: min(T, p1 * (D - 1))
     int radius;      // labels beyond which the truncation dominates: ceil(T/p1) - 1
     int npaths;
+    int lanes;       // lanes per scan path for 32/64-label strides (4 or 8; autotuned)
+};
+
+// Launch shapes chosen per image shape by the autotuner.
+struct Tuning {
+    int lanes = 8;   // aggregation: lanes per scan path (4 or 8)
 };
 
 struct SeedArgs {
@@ -119,6 +125,7 @@ int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg);
 // Enqueues the whole matcher for one pair on stream s, with its scratch at `workspace`
 // (at least make_layout(...).total bytes).
 mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *workspace,
-                        cudaStream_t s, const StageHook *hook, const StageSink *dbg);
+                        cudaStream_t s, const StageHook *hook, const StageSink *dbg,
+                        const Tuning &tune = Tuning());
 
 }  // namespace mpv

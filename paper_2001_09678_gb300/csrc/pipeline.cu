@@ -131,7 +131,7 @@ int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg)
 }
 
 mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, cudaStream_t s,
-                        const StageHook *hook, const StageSink *dbg)
+                        const StageHook *hook, const StageSink *dbg, const Tuning &tune)
 {
     Geometry g;
     make_geometry(p, job.W, job.H, job.D, g);
@@ -191,6 +191,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
         a.p1 = (int)(p.p1 < Teff ? p.p1 : Teff);
         a.radius = a.p1 > 0 ? (int)((Teff + a.p1 - 1) / a.p1) - 1 : 0;
         a.npaths = p.num_paths;
+        a.lanes = tune.lanes;
         for (int v = 0; v < nviews; ++v) {
             ViewLevel &vl = a.v[v];
             vl.I0 = I0[v][l];

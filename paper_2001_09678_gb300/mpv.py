@@ -70,7 +70,7 @@ EXPORTS = [
     "mpv_match_host", "mpv_match_batch", "mpv_load_proposal_weights", "mpv_sync",
     "mpv_workspace_bytes", "mpv_set_workspace_limit", "mpv_debug_stage", "mpv_level_info",
     "mpv_status_string", "mpv_destroy", "mpv_profile_enable", "mpv_profile_read",
-    "mpv_match_noalloc",
+    "mpv_match_noalloc", "mpv_autotune",
 ]
 MPV_NOALLOC_SCRATCH_BYTES = 64 << 20
 MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
     L.mpv_profile_enable.argtypes = [ctx, i32]
     L.mpv_profile_read.argtypes = [ctx, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
     L.mpv_match_noalloc.argtypes = [pp, vp, vp, i32, i32, i32, vp, i32, vp]
+    L.mpv_autotune.argtypes = [ctx, C.POINTER(mpv_pair), C.POINTER(i32)]
     L.mpv_destroy.argtypes = [ctx]
     L.mpv_destroy.restype = None
     for name in EXPORTS:
@@ -190,9 +191,7 @@ def mpv_match_host(ctx, left, right, disp, stream=None) -> None:
                                  _stream(stream)), "mpv_match_host")
 
 
-def mpv_match_batch(ctx, pairs, stream=None) -> None:
-    """pairs: list of dicts with left, right, disp tensors and optional max_disparity,
-    disp_right."""
+def _pairs(pairs):
     arr = (mpv_pair * len(pairs))()
     for i, q in enumerate(pairs):
         left = q["left"]
@@ -205,7 +204,22 @@ def mpv_match_batch(ctx, pairs, stream=None) -> None:
         arr[i].disp_pitch = q["disp"].stride(-2)
         dr = q.get("disp_right")
         arr[i].disp_right = dr.data_ptr() if dr is not None else None
+    return arr
+
+
+def mpv_match_batch(ctx, pairs, stream=None) -> None:
+    """pairs: list of dicts with left, right, disp tensors and optional max_disparity,
+    disp_right."""
+    arr = _pairs(pairs)
     _check(load().mpv_match_batch(ctx, arr, len(pairs), _stream(stream)), "mpv_match_batch")
+
+
+def mpv_autotune(ctx, pair) -> int:
+    """Tunes the launch shapes for pair's shape; returns the chosen lanes per path."""
+    arr = _pairs([pair])
+    lanes = C.c_int32()
+    _check(load().mpv_autotune(ctx, arr, C.byref(lanes)), "mpv_autotune")
+    return lanes.value
 
 
 def mpv_load_proposal_weights(ctx, path: str) -> None:
