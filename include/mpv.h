@@ -161,6 +161,49 @@ mpv_status mpv_debug_stage(mpv_ctx *ctx, const uint8_t *left, const uint8_t *rig
 mpv_status mpv_level_info(const mpv_ctx *ctx, int32_t width, int32_t height, int32_t level,
                           int32_t *w, int32_t *h, int32_t *range, int32_t *window);
 
+/* ---- Serving: continuous batching over camera streams (spec serving loop) ------
+ *
+ * A server owns, per registered camera, resident device state (a matcher context whose
+ * workspace keeps that frame size's pyramid levels and volumes allocated between frames,
+ * device copies of the pair and map, pinned staging, a stream).  Frames are submitted
+ * from HOST buffers and wait in a per-camera FIFO.  mpv_server_poll retires finished
+ * frames (copying their maps to the caller's buffers) and admits waiting frames, oldest
+ * first, while fewer than max_inflight frames run and the resident memory of the
+ * admitted cameras fits hbm_budget (0 = no limit); idle cameras are evicted least
+ * recently used first to make room.  Admitted frames of different cameras run
+ * concurrently on the GPU.  The server is used from one host thread; nothing blocks on
+ * the GPU.  Results equal mpv_match of the same pair alone.                           */
+typedef struct mpv_server mpv_server;
+
+typedef struct {
+    uint64_t request_id;
+    int32_t camera;
+    mpv_status status;      /* MPV_ERR_OOM: the camera cannot fit the budget at all    */
+    double t_submit_ms;     /* host steady clock at submit                              */
+    double t_start_ms;      /* admitted: copies and kernels enqueued                     */
+    double t_done_ms;       /* the map reached pinned host memory (stream callback)      */
+} mpv_completion;
+
+mpv_status mpv_server_create(int device, const mpv_params *params, size_t hbm_budget,
+                             int32_t max_inflight, mpv_server **out);
+/* Registers a camera's frame geometry and range (validated as for mpv_match). */
+mpv_status mpv_server_add_camera(mpv_server *srv, int32_t camera, int32_t width,
+                                 int32_t height, int32_t max_disparity);
+/* Queues a frame.  left/right (rows `pitch` bytes apart) and disp (rows disp_pitch
+ * elements apart) are host buffers that must stay valid until the frame completes.   */
+mpv_status mpv_server_submit(mpv_server *srv, int32_t camera, const uint8_t *left,
+                             const uint8_t *right, int32_t pitch, uint16_t *disp,
+                             int32_t disp_pitch, uint64_t request_id);
+/* Retires and admits (see above); writes up to max completions to out, *n = count. */
+mpv_status mpv_server_poll(mpv_server *srv, mpv_completion *out, int32_t max, int32_t *n);
+/* Current in-flight and waiting frames, resident bytes, evictions so far and the largest
+ * number of frames that were in flight at once.  Any output may be NULL.              */
+mpv_status mpv_server_stats(const mpv_server *srv, int32_t *inflight, int32_t *waiting,
+                            size_t *resident_bytes, uint64_t *evictions,
+                            int32_t *peak_inflight);
+/* Waits for in-flight frames, then releases everything; NULL is accepted. */
+void mpv_server_destroy(mpv_server *srv);
+
 /* Stages reported by the profiler. */
 #define MPV_STAGE_PYRAMID 0     /* mirroring and 2x2 down-sampling                      */
 #define MPV_STAGE_SEED 1        /* per-pixel windows of the finer levels                 */

@@ -51,6 +51,17 @@ class mpv_params(C.Structure):
     ]
 
 
+class mpv_completion(C.Structure):
+    _fields_ = [
+        ("request_id", C.c_uint64),
+        ("camera", C.c_int32),
+        ("status", C.c_int),
+        ("t_submit_ms", C.c_double),
+        ("t_start_ms", C.c_double),
+        ("t_done_ms", C.c_double),
+    ]
+
+
 class mpv_pair(C.Structure):
     _fields_ = [
         ("left", C.c_void_p),
@@ -70,7 +81,8 @@ EXPORTS = [
     "mpv_match_host", "mpv_match_batch", "mpv_load_proposal_weights", "mpv_sync",
     "mpv_workspace_bytes", "mpv_set_workspace_limit", "mpv_debug_stage", "mpv_level_info",
     "mpv_status_string", "mpv_destroy", "mpv_profile_enable", "mpv_profile_read",
-    "mpv_match_noalloc", "mpv_autotune",
+    "mpv_match_noalloc", "mpv_autotune", "mpv_server_create", "mpv_server_add_camera",
+    "mpv_server_submit", "mpv_server_poll", "mpv_server_stats", "mpv_server_destroy",
 ]
 MPV_NOALLOC_SCRATCH_BYTES = 64 << 20
 MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
@@ -107,11 +119,19 @@ def load(path: str = LIB_PATH):
     L.mpv_profile_read.argtypes = [ctx, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
     L.mpv_match_noalloc.argtypes = [pp, vp, vp, i32, i32, i32, vp, i32, vp]
     L.mpv_autotune.argtypes = [ctx, C.POINTER(mpv_pair), C.POINTER(i32)]
+    L.mpv_server_create.argtypes = [C.c_int, pp, C.c_size_t, i32, C.POINTER(C.c_void_p)]
+    L.mpv_server_add_camera.argtypes = [vp, i32, i32, i32, i32]
+    L.mpv_server_submit.argtypes = [vp, i32, vp, vp, i32, vp, i32, C.c_uint64]
+    L.mpv_server_poll.argtypes = [vp, C.POINTER(mpv_completion), i32, C.POINTER(i32)]
+    L.mpv_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_size_t),
+                                   C.POINTER(C.c_uint64), C.POINTER(i32)]
+    L.mpv_server_destroy.argtypes = [vp]
     L.mpv_destroy.argtypes = [ctx]
     L.mpv_destroy.restype = None
+    L.mpv_server_destroy.restype = None
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("mpv_status_string", "mpv_destroy"):
+        if name not in ("mpv_status_string", "mpv_destroy", "mpv_server_destroy"):
             f.restype = C.c_int
     _lib = L
     return L
@@ -275,6 +295,47 @@ def mpv_match_noalloc(params: mpv_params, left, right, disp, stream=None) -> Non
     _check(load().mpv_match_noalloc(C.byref(params), _ptr(left), _ptr(right), W, H,
                                     left.stride(-2), _ptr(disp), disp.stride(-2),
                                     _stream(stream)), "mpv_match_noalloc")
+
+
+def mpv_server_create(params: mpv_params, hbm_budget: int = 0, max_inflight: int = 8,
+                      device: int = 0):
+    h = C.c_void_p()
+    _check(load().mpv_server_create(device, C.byref(params), hbm_budget, max_inflight,
+                                    C.byref(h)), "mpv_server_create")
+    return h
+
+
+def mpv_server_add_camera(srv, camera: int, width: int, height: int, max_disparity: int):
+    _check(load().mpv_server_add_camera(srv, camera, width, height, max_disparity),
+           "mpv_server_add_camera")
+
+
+def mpv_server_submit(srv, camera: int, left, right, disp, request_id: int):
+    """left, right: uint8 numpy arrays (kept alive by the caller until completion);
+    disp: uint16 numpy array receiving the map."""
+    _check(load().mpv_server_submit(srv, camera, C.c_void_p(left.ctypes.data),
+                                    C.c_void_p(right.ctypes.data), left.strides[0],
+                                    C.c_void_p(disp.ctypes.data), disp.strides[0] // 2,
+                                    request_id), "mpv_server_submit")
+
+
+def mpv_server_poll(srv, max_completions: int = 64):
+    out = (mpv_completion * max_completions)()
+    n = C.c_int32()
+    _check(load().mpv_server_poll(srv, out, max_completions, C.byref(n)), "mpv_server_poll")
+    return [out[i] for i in range(n.value)]
+
+
+def mpv_server_stats(srv):
+    a, b, c, d, e = C.c_int32(), C.c_int32(), C.c_size_t(), C.c_uint64(), C.c_int32()
+    _check(load().mpv_server_stats(srv, C.byref(a), C.byref(b), C.byref(c), C.byref(d),
+                                   C.byref(e)), "mpv_server_stats")
+    return dict(inflight=a.value, waiting=b.value, resident_bytes=c.value, evictions=d.value,
+                peak_inflight=e.value)
+
+
+def mpv_server_destroy(srv) -> None:
+    load().mpv_server_destroy(srv)
 
 
 def mpv_destroy(ctx) -> None:
