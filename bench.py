@@ -346,6 +346,59 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_batch64(args):
+    """Throughput of the 64-pair mixed-resolution batch (one cached CUDA graph)."""
+    import multiprocessing as mp
+    import torch
+    from paper_2001_09678_gb300 import synth
+    specs = synth.mixed_batch_specs()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        images = pool.map(_gen_pair, specs)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2001_09678_gb300 import mpv
+    dev = torch.device("cuda", 0)
+    pairs = []
+    units = 0
+    for (L, R), (_seed, W, H, D) in zip(images, specs):
+        pairs.append(dict(left=torch.from_numpy(L).to(dev), right=torch.from_numpy(R).to(dev),
+                          disp=torch.empty((H, W), dtype=torch.int16, device=dev),
+                          max_disparity=D))
+        units += W * H * D
+    ctx = mpv.mpv_create(0)
+    mpv.mpv_set_params(ctx, mpv.mpv_default_params(**PARAMS))
+    stream = torch.cuda.current_stream(dev)
+    t = time.perf_counter()
+    mpv.mpv_match_batch(ctx, pairs, stream)     # autotune + capture
+    mpv.mpv_sync(ctx)
+    setup_s = time.perf_counter() - t
+    for _ in range(args.warmup):
+        mpv.mpv_match_batch(ctx, pairs, stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mpv.mpv_match_batch(ctx, pairs, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    mpv.mpv_destroy(ctx)
+    print(json.dumps({
+        "metric": "Mdisp-evals/s, 64-pair mixed batch", "value": round(units / ms / 1e3, 1),
+        "unit": UNIT, "ms_per_batch": round(ms, 3), "pairs_per_s": round(64e3 / ms, 1),
+        "steps": args.steps, "warmup": args.warmup, "setup_s": round(setup_s, 2),
+        "config": {"workload": "16x640x480 D64 + 32x1280x720 D128 + 16x1920x1080 D192, "
+                               "3 scales, 8 paths, LR, one CUDA graph per batch"},
+    }), flush=True)
+
+
+def _gen_pair(spec):
+    from paper_2001_09678_gb300 import synth
+    seed, W, H, D = spec
+    L, R, _ = synth.slanted_pair(W, H, seed=seed, d_max=min(120.0, D - 8.0))
+    return L, R
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,9 +406,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("mine", "reference"), default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("frame", "batch64"), default="frame",
+                    help="frame: the 1280x720 D=128 pair (default); batch64: the mixed batch")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "batch64" and args.impl == "mine":
+        run_batch64(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

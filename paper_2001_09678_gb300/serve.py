@@ -59,8 +59,22 @@ def frame_pools(sizes, per_size: int, workers: int | None = None):
     return pools
 
 
+def _warm(srv, cams, pools):
+    """One frame per camera, not timed: makes every camera's state resident."""
+    keep = []
+    for cid, W, H, D in cams:
+        L, R = pools[(W, H, D)][0]
+        disp = np.empty((H, W), np.uint16)
+        keep.append(disp)
+        mpv.mpv_server_submit(srv, cid, L, R, disp, (1 << 62) + cid)
+    done = 0
+    while done < len(cams):
+        done += len(mpv.mpv_server_poll(srv))
+        time.sleep(1e-4)
+
+
 def run(cams, pools, seconds=5.0, hz=30.0, budget=0, max_inflight=8, params=None,
-        keep_outputs=False, seed=0):
+        keep_outputs=False, seed=0, warm=True):
     """Serves every camera's arrivals for `seconds`; returns latencies and stats."""
     params = params or mpv.mpv_default_params()
     srv = mpv.mpv_server_create(params, hbm_budget=budget, max_inflight=max_inflight)
@@ -70,6 +84,8 @@ def run(cams, pools, seconds=5.0, hz=30.0, budget=0, max_inflight=8, params=None
             mpv.mpv_server_add_camera(srv, cid, W, H, D)
             for k, t in enumerate(arrivals(cid, hz, seconds, seed)):
                 events.append((t, cid, k, W, H, D))
+        if warm and budget == 0:
+            _warm(srv, cams, pools)
         events.sort()
         outputs = {}
         pending = {}
