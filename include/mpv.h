@@ -204,6 +204,48 @@ mpv_status mpv_server_stats(const mpv_server *srv, int32_t *inflight, int32_t *w
 /* Waits for in-flight frames, then releases everything; NULL is accepted. */
 void mpv_server_destroy(mpv_server *srv);
 
+/* ---- Learned window proposal: network kernels (training and inference) -------------
+ *
+ * The learned proposal (spec extension; the paper has none) replaces the pyramid's
+ * window seeding at the finest level by a small CNN evaluated at the top level: six
+ * 3x3 convolutions, zero padding, 2 + D_top input channels (the top level's left and
+ * right images and its full-range cost slice), 32 hidden channels with ReLU, one output
+ * channel (disparity / D).  Activations and weights are BF16 (__nv_bfloat16 in device
+ * memory, passed as void *), accumulation and gradients FP32.  Tensors are NCHW, device
+ * pointers, asynchronous on cuda_stream.  Invalid sizes return MPV_ERR_INVALID_ARG.   */
+
+/* out = conv3x3(in, weight[cout][cin][3][3]) + bias, optional ReLU; in is BF16, or FP32
+ * when in_f32 = 1; cout is 32 or 1; out_bf16 and/or out_f32 receive the result.       */
+mpv_status mpv_cnn_conv3x3(const void *in, int32_t in_f32, int32_t n, int32_t cin, int32_t h,
+                           int32_t w, const void *weight, const float *bias, int32_t cout,
+                           int32_t relu, void *out_bf16, float *out_f32, void *cuda_stream);
+/* dweight[cout][cin][3][3] += sum over n,y,x of grad[n][co][y][x] in[n][ci][y+ky-1][x+kx-1];
+ * dbias[cout] += sum of grad (dbias may be NULL).  Accumulates: zero them first.      */
+mpv_status mpv_cnn_conv3x3_wgrad(const void *in, int32_t n, int32_t cin, const float *grad,
+                                 int32_t cout, int32_t h, int32_t w, float *dweight,
+                                 float *dbias, void *cuda_stream);
+/* out[ci][co][2-ky][2-kx] = weight[co][ci][ky][kx] (BF16): the backward-data weights. */
+mpv_status mpv_cnn_flip_transpose(const void *weight, int32_t cout, int32_t cin, void *out,
+                                  void *cuda_stream);
+/* out = grad where act > 0 else 0 (ReLU backward; act BF16). */
+mpv_status mpv_cnn_relu_backward(const float *grad, const void *act, float *out, int64_t count,
+                                 void *cuda_stream);
+/* Huber loss with threshold delta, mean over count: grad = dloss/dpred; *loss (may be
+ * NULL) is incremented by the mean loss.                                              */
+mpv_status mpv_cnn_huber(const float *pred, const float *target, float delta, int64_t count,
+                         float *grad, float *loss, void *cuda_stream);
+/* One Adam step (bias-corrected, step >= 1) on FP32 weights; refreshes weight_bf16 when
+ * not NULL.                                                                           */
+mpv_status mpv_cnn_adam(float *weight, const float *grad, float *m, float *v, int64_t count,
+                        float lr, float beta1, float beta2, float eps, int32_t step,
+                        void *weight_bf16, void *cuda_stream);
+mpv_status mpv_cnn_to_bf16(const float *in, void *out, int64_t count, void *cuda_stream);
+/* Training target: mean of each factor x factor block of a full-resolution disparity
+ * map, divided by max_disparity, at ceil(width/factor) x ceil(height/factor).        */
+mpv_status mpv_cnn_target(const uint16_t *disp, int32_t disp_pitch, int32_t width,
+                          int32_t height, int32_t factor, int32_t max_disparity, float *target,
+                          void *cuda_stream);
+
 /* Stages reported by the profiler. */
 #define MPV_STAGE_PYRAMID 0     /* mirroring and 2x2 down-sampling                      */
 #define MPV_STAGE_SEED 1        /* per-pixel windows of the finer levels                 */

@@ -83,6 +83,9 @@ EXPORTS = [
     "mpv_status_string", "mpv_destroy", "mpv_profile_enable", "mpv_profile_read",
     "mpv_match_noalloc", "mpv_autotune", "mpv_server_create", "mpv_server_add_camera",
     "mpv_server_submit", "mpv_server_poll", "mpv_server_stats", "mpv_server_destroy",
+    "mpv_cnn_conv3x3", "mpv_cnn_conv3x3_wgrad", "mpv_cnn_flip_transpose",
+    "mpv_cnn_relu_backward", "mpv_cnn_huber", "mpv_cnn_adam", "mpv_cnn_to_bf16",
+    "mpv_cnn_target",
 ]
 MPV_NOALLOC_SCRATCH_BYTES = 64 << 20
 MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
@@ -126,6 +129,17 @@ def load(path: str = LIB_PATH):
     L.mpv_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_size_t),
                                    C.POINTER(C.c_uint64), C.POINTER(i32)]
     L.mpv_server_destroy.argtypes = [vp]
+    fp = C.POINTER(C.c_float)
+    i64 = C.c_int64
+    L.mpv_cnn_conv3x3.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp, i32, i32, vp, vp, vp]
+    L.mpv_cnn_conv3x3_wgrad.argtypes = [vp, i32, i32, vp, i32, i32, i32, vp, vp, vp]
+    L.mpv_cnn_flip_transpose.argtypes = [vp, i32, i32, vp, vp]
+    L.mpv_cnn_relu_backward.argtypes = [vp, vp, vp, i64, vp]
+    L.mpv_cnn_huber.argtypes = [vp, vp, C.c_float, i64, vp, vp, vp]
+    L.mpv_cnn_adam.argtypes = [vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float, C.c_float,
+                               i32, vp, vp]
+    L.mpv_cnn_to_bf16.argtypes = [vp, vp, i64, vp]
+    L.mpv_cnn_target.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp]
     L.mpv_destroy.argtypes = [ctx]
     L.mpv_destroy.restype = None
     L.mpv_server_destroy.restype = None
@@ -336,6 +350,57 @@ def mpv_server_stats(srv):
 
 def mpv_server_destroy(srv) -> None:
     load().mpv_server_destroy(srv)
+
+
+def mpv_cnn_conv3x3(x, weight_bf16, bias, cout, relu, out_bf16=None, out_f32=None,
+                    stream=None):
+    """x: [N, Cin, H, W] bfloat16 or float32 CUDA tensor; weight [cout, Cin, 3, 3] bf16."""
+    N, Cin, H, W = x.shape
+    in_f32 = 1 if x.dtype.is_floating_point and x.element_size() == 4 else 0
+    _check(load().mpv_cnn_conv3x3(_ptr(x), in_f32, N, Cin, H, W, _ptr(weight_bf16), _ptr(bias),
+                                  cout, int(relu), _ptr(out_bf16), _ptr(out_f32),
+                                  _stream(stream)), "mpv_cnn_conv3x3")
+
+
+def mpv_cnn_conv3x3_wgrad(x_bf16, grad, dweight, dbias, stream=None):
+    N, Cin, H, W = x_bf16.shape
+    _check(load().mpv_cnn_conv3x3_wgrad(_ptr(x_bf16), N, Cin, _ptr(grad), grad.shape[1], H, W,
+                                        _ptr(dweight), _ptr(dbias), _stream(stream)),
+           "mpv_cnn_conv3x3_wgrad")
+
+
+def mpv_cnn_flip_transpose(weight_bf16, out, stream=None):
+    cout, cin = weight_bf16.shape[0], weight_bf16.shape[1]
+    _check(load().mpv_cnn_flip_transpose(_ptr(weight_bf16), cout, cin, _ptr(out),
+                                         _stream(stream)), "mpv_cnn_flip_transpose")
+
+
+def mpv_cnn_relu_backward(grad, act_bf16, out, stream=None):
+    _check(load().mpv_cnn_relu_backward(_ptr(grad), _ptr(act_bf16), _ptr(out), grad.numel(),
+                                        _stream(stream)), "mpv_cnn_relu_backward")
+
+
+def mpv_cnn_huber(pred, target, delta, grad, loss=None, stream=None):
+    _check(load().mpv_cnn_huber(_ptr(pred), _ptr(target), float(delta), pred.numel(),
+                                _ptr(grad), _ptr(loss), _stream(stream)), "mpv_cnn_huber")
+
+
+def mpv_cnn_adam(weight, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8,
+                 weight_bf16=None, stream=None):
+    _check(load().mpv_cnn_adam(_ptr(weight), _ptr(grad), _ptr(m), _ptr(v), weight.numel(),
+                               float(lr), float(beta1), float(beta2), float(eps), int(step),
+                               _ptr(weight_bf16), _stream(stream)), "mpv_cnn_adam")
+
+
+def mpv_cnn_to_bf16(x, out, stream=None):
+    _check(load().mpv_cnn_to_bf16(_ptr(x), _ptr(out), x.numel(), _stream(stream)),
+           "mpv_cnn_to_bf16")
+
+
+def mpv_cnn_target(disp, factor, max_disparity, target, stream=None):
+    H, W = disp.shape[-2], disp.shape[-1]
+    _check(load().mpv_cnn_target(_ptr(disp), disp.stride(-2), W, H, factor, max_disparity,
+                                 _ptr(target), _stream(stream)), "mpv_cnn_target")
 
 
 def mpv_destroy(ctx) -> None:

@@ -1,0 +1,117 @@
+"""The learned proposal's BF16/FP32 network kernels against the float64 CNN oracle.
+
+The oracle is fed the same BF16-rounded inputs and weights the device holds, so the
+remaining differences come from FP32 accumulation (and, through the network, from BF16
+rounding of activations that sit near a rounding boundary): the tolerances below are
+stated relative to the magnitude of the summed terms.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import cnn_ref  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def m():
+    from paper_2001_09678_gb300 import build, mpv
+    build.build()
+    mpv.load()
+    return mpv
+
+
+def _bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda().to(torch.bfloat16)
+
+
+def test_conv_forward_matches_oracle(m):
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(2, 34, 37, 45)).astype(np.float32)
+    w = (rng.normal(size=(32, 34, 3, 3)) * 0.1).astype(np.float32)
+    b = rng.normal(size=32).astype(np.float32)
+    out = torch.empty((2, 32, 37, 45), dtype=torch.float32, device="cuda")
+    m.mpv_cnn_conv3x3(_bf(x), _bf(w), torch.from_numpy(b).cuda(), 32, True, out_f32=out)
+    xq, wq = cnn_ref.bf16(x), cnn_ref.bf16(w)
+    want = np.maximum(cnn_ref.conv3x3(xq, wq, b), 0)
+    scale = cnn_ref.conv3x3(np.abs(xq), np.abs(wq)) + np.abs(b)[None, :, None, None]
+    assert np.all(np.abs(out.cpu().numpy() - want) <= 1e-5 * scale + 1e-6)
+
+
+def test_conv_fp32_input_one_channel_out(m):
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(1, 32, 20, 17)).astype(np.float32)
+    w = (rng.normal(size=(1, 32, 3, 3)) * 0.1).astype(np.float32)
+    out = torch.empty((1, 1, 20, 17), dtype=torch.float32, device="cuda")
+    m.mpv_cnn_conv3x3(torch.from_numpy(x).cuda(), _bf(w), None, 1, False, out_f32=out)
+    wq = cnn_ref.bf16(w)
+    want = cnn_ref.conv3x3(x.astype(np.float64), wq)
+    scale = cnn_ref.conv3x3(np.abs(x.astype(np.float64)), np.abs(wq))
+    assert np.all(np.abs(out.cpu().numpy() - want) <= 1e-5 * scale + 1e-6)
+
+
+def test_weight_gradient_matches_oracle(m):
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(2, 32, 40, 36)).astype(np.float32)
+    g = rng.normal(size=(2, 32, 40, 36)).astype(np.float32)
+    dw = torch.zeros((32, 32, 3, 3), dtype=torch.float32, device="cuda")
+    db = torch.zeros(32, dtype=torch.float32, device="cuda")
+    m.mpv_cnn_conv3x3_wgrad(_bf(x), torch.from_numpy(g).cuda(), dw, db)
+    xq = cnn_ref.bf16(x)
+    _, want_w, want_b = cnn_ref.conv3x3_backward(xq, np.zeros((32, 32, 3, 3)), g.astype(np.float64))
+    _, scale_w, scale_b = cnn_ref.conv3x3_backward(np.abs(xq), np.zeros((32, 32, 3, 3)),
+                                                   np.abs(g).astype(np.float64))
+    assert np.all(np.abs(dw.cpu().numpy() - want_w) <= 1e-5 * scale_w + 1e-6)
+    assert np.all(np.abs(db.cpu().numpy() - want_b) <= 1e-5 * scale_b + 1e-6)
+
+
+def test_network_gradients_match_oracle(m):
+    from paper_2001_09678_gb300 import learn
+    rng = np.random.default_rng(3)
+    layers = learn.init_weights(34, seed=4)
+    net = learn.Net(layers)
+    x = rng.uniform(-0.5, 0.5, size=(2, 34, 24, 20)).astype(np.float32)
+    t = rng.uniform(0, 1, size=(2, 1, 24, 20)).astype(np.float32)
+    xb = _bf(x)
+    pred, acts = net.forward(xb)
+    grad = torch.empty_like(pred)
+    loss = torch.zeros(1, device="cuda")
+    m.mpv_cnn_huber(pred, torch.from_numpy(t).cuda(), 1.0 / 128, grad, loss)
+    grads = net.backward(acts, grad)
+    p_ref, acts_ref = cnn_ref.forward(x, layers, round_bf16=True)
+    assert np.allclose(pred.cpu().numpy(), p_ref, rtol=1e-3, atol=1e-3)
+    _, g_ref = cnn_ref.huber(pred.cpu().numpy().astype(np.float64), t, 1.0 / 128)
+    grads_ref = cnn_ref.backward(acts_ref, layers, g_ref, round_bf16=True)
+    for i, ((dw, db), (rw, rb)) in enumerate(zip(grads, grads_ref)):
+        dw, db = dw.cpu().numpy(), db.cpu().numpy()
+        assert np.linalg.norm(dw - rw) <= 1e-2 * np.linalg.norm(rw) + 1e-9, i
+        assert np.linalg.norm(db - rb) <= 1e-2 * np.linalg.norm(rb) + 1e-9, i
+
+
+def test_huber_and_adam(m):
+    p = torch.tensor([0.0, 0.1, 2.0, -3.0], device="cuda")
+    t = torch.zeros(4, device="cuda")
+    g = torch.empty(4, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    m.mpv_cnn_huber(p, t, 0.5, g, loss)
+    assert np.allclose(g.cpu().numpy(), np.array([0, 0.2, 1, -1]) / 4)
+    assert np.isclose(loss.item(), (0.01 + 1.75 + 2.75) / 4)
+    w = torch.tensor([1.0, -2.0], device="cuda")
+    gr = torch.tensor([0.5, -0.25], device="cuda")
+    mm, vv = torch.zeros(2, device="cuda"), torch.zeros(2, device="cuda")
+    m.mpv_cnn_adam(w, gr, mm, vv, 0.1, 1)
+    # first bias-corrected Adam step moves each weight by lr * sign(g) (up to eps)
+    assert np.allclose(w.cpu().numpy(), [0.9, -1.9], atol=1e-6)
+
+
+def test_training_reduces_loss(m):
+    from paper_2001_09678_gb300 import learn
+    rng = np.random.default_rng(5)
+    net = learn.Net(learn.init_weights(34, seed=6))
+    xn = rng.uniform(-0.5, 0.5, size=(4, 34, 32, 32)).astype(np.float32)
+    x = _bf(xn)
+    # a target the network can fit: an affine function of the first input channel
+    t = torch.from_numpy((0.5 + 0.5 * xn[:, :1]).astype(np.float32)).cuda()
+    losses = [net.train_step(x, t, 3e-3, 1.0 / 128).item() for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0]
