@@ -79,14 +79,22 @@ def test_network_gradients_match_oracle(m):
     loss = torch.zeros(1, device="cuda")
     m.mpv_cnn_huber(pred, torch.from_numpy(t).cuda(), 1.0 / 128, grad, loss)
     grads = net.backward(acts, grad)
-    p_ref, acts_ref = cnn_ref.forward(x, layers, round_bf16=True)
+    # forward: the device stores every hidden activation in BF16; a value whose FP32 and
+    # float64 sums straddle a BF16 rounding boundary rounds one BF16 ulp (2^-8 relative)
+    # differently, and that propagates: agreement to 1e-3 of the output scale
+    p_ref, _ = cnn_ref.forward(x, layers, round_bf16=True)
     assert np.allclose(pred.cpu().numpy(), p_ref, rtol=1e-3, atol=1e-3)
+    # backward: fed the device's own stored activations (same ReLU masks), the float64
+    # chain rule must agree with the FP32 kernels to FP32 accumulation error
+    acts_dev = [a.float().cpu().numpy().astype(np.float64) for a in acts]
     _, g_ref = cnn_ref.huber(pred.cpu().numpy().astype(np.float64), t, 1.0 / 128)
-    grads_ref = cnn_ref.backward(acts_ref, layers, g_ref, round_bf16=True)
+    grads_ref = cnn_ref.backward(acts_dev, layers, g_ref, round_bf16=True)
+    errs = []
     for i, ((dw, db), (rw, rb)) in enumerate(zip(grads, grads_ref)):
         dw, db = dw.cpu().numpy(), db.cpu().numpy()
-        assert np.linalg.norm(dw - rw) <= 1e-2 * np.linalg.norm(rw) + 1e-9, i
-        assert np.linalg.norm(db - rb) <= 1e-2 * np.linalg.norm(rb) + 1e-9, i
+        errs.append((np.linalg.norm(dw - rw) / np.linalg.norm(rw),
+                     np.linalg.norm(db - rb) / (np.linalg.norm(rb) + 1e-30)))
+    assert all(ew <= 1e-4 and eb <= 1e-4 for ew, eb in errs), errs
 
 
 def test_huber_and_adam(m):
