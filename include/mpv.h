@@ -133,8 +133,29 @@ mpv_status mpv_match_batch(mpv_ctx *ctx, const mpv_pair *pairs, int32_t n, void 
  * aggregation (4 or 8).  Synchronous.  Results do not depend on the choice.          */
 mpv_status mpv_autotune(mpv_ctx *ctx, const mpv_pair *pair, int32_t *lanes);
 
-/* Loads the learned-proposal network weights (used when proposal = LEARNED). */
+/* Loads the learned-proposal network (file written by paper_2001_09678_gb300/learn.py:
+ * "MPVP", version 1, six layers of 3x3 convolutions, FP32 weights stored, converted to
+ * BF16 on load).  With proposal = LEARNED (num_scales >= 2), a match computes the top
+ * pyramid level's full-range cost, runs the network on it, and searches at the finest
+ * level the window of `window` labels (default 17, i.e. centre +- 8) around the
+ * prediction instead of seeding the intermediate levels.  The network's input channel
+ * count must equal 2 + ceil(D / 2^(S-1)) (MPV_ERR_INVALID_ARG at match time
+ * otherwise).  Invalid files return MPV_ERR_INVALID_ARG and keep the loaded network.  */
 mpv_status mpv_load_proposal_weights(mpv_ctx *ctx, const char *path);
+
+/* Network input of one pair, for training: the top pyramid level of `view` (0 = left
+ * view, 1 = the mirrored, swapped pair) as 2 + D_top BF16 planes of W_top x H_top:
+ * left/255 - 1/2, right/255 - 1/2, then the cost slice C(k)/255 for every label k.
+ * Uses the context's pyramid parameters.  Asynchronous.                              */
+mpv_status mpv_proposal_features(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                 int32_t width, int32_t height, int32_t pitch, int32_t view,
+                                 void *out, void *cuda_stream);
+
+/* Of the last mpv_match with the learned proposal (read after mpv_sync): the pixels
+ * whose winning label sits on their window's edge while the range continues past it,
+ * and the pixels matched (both views).  A high ratio means the windows missed: the
+ * caller should match the pair again with the pyramid (the fallback).                 */
+mpv_status mpv_proposal_stats(const mpv_ctx *ctx, uint64_t *edge_hits, uint64_t *pixels);
 
 /* Waits for the context's last submitted work and returns any latched device error. */
 mpv_status mpv_sync(mpv_ctx *ctx);

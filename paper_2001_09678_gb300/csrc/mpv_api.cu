@@ -44,6 +44,10 @@ struct mpv_ctx {
     };
     std::vector<Graph> graphs;
     std::map<uint64_t, Tuning> tuning;
+    // learned proposal
+    ProposalNet net;
+    void *net_mem = nullptr;
+    unsigned long long *edge_host = nullptr;   // pinned: window-edge hits, pixels
 };
 
 namespace {
@@ -171,7 +175,8 @@ mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
     cudaStreamSynchronize(ctx->last_stream);
     Geometry g;
     make_geometry(ctx->p, job.W, job.H, job.D, g);
-    st = ensure_workspace(ctx, make_layout(g, views_needed(ctx->p, job, nullptr)).total);
+    st = ensure_workspace(ctx, make_layout(g, views_needed(ctx->p, job, nullptr),
+                                           ctx->p.proposal == MPV_PROPOSAL_LEARNED).total);
     if (st != MPV_OK) return st;
     cudaStream_t s = ctx->workers[0];
     cudaEvent_t e0, e1;
@@ -183,11 +188,11 @@ mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
     for (int c : cands) {
         Tuning t;
         t.lanes = c;
-        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t);
+        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t, &ctx->net);
         float tot = 0.f;
         for (int r = 0; r < 2; ++r) {
             cudaEventRecord(e0, s);
-            enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t);
+            enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t, &ctx->net);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -234,7 +239,8 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
         worker[i] = r % nw;
         Geometry g;
         make_geometry(ctx->p, jobs[i].W, jobs[i].H, jobs[i].D, g);
-        const size_t b = make_layout(g, views_needed(ctx->p, jobs[i], nullptr)).total;
+        const size_t b = make_layout(g, views_needed(ctx->p, jobs[i], nullptr),
+                                     ctx->p.proposal == MPV_PROPOSAL_LEARNED).total;
         wbytes[worker[i]] = std::max(wbytes[worker[i]], b);
     }
     size_t total = 0;
@@ -288,7 +294,7 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
         const int i = order[r];
         const int w = worker[i];
         est = enqueue_pair(ctx->p, jobs[i], (uint8_t *)ctx->bws + woff[w], ctx->workers[w],
-                           nullptr, nullptr, tune[i]);
+                           nullptr, nullptr, tune[i], &ctx->net);
     }
     for (int w = 0; w < nw; ++w) {
         cudaEventRecord(ctx->joins[w], ctx->workers[w]);
@@ -320,14 +326,31 @@ mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const Stage
 {
     Geometry g;
     make_geometry(ctx->p, job.W, job.H, job.D, g);
-    const Layout L = make_layout(g, views_needed(ctx->p, job, dbg));
+    const Layout L = make_layout(g, views_needed(ctx->p, job, dbg),
+                                 ctx->p.proposal == MPV_PROPOSAL_LEARNED);
     const mpv_status st = ensure_workspace(ctx, L.total);
     if (st != MPV_OK) return st;
     StageHook hook{hook_begin, hook_end, ctx};
     Tuning t;
     const auto it = ctx->tuning.find(shape_key(ctx->p, job.W, job.H, job.D));
     if (it != ctx->tuning.end()) t = it->second;
-    return enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t);
+    const bool learned = ctx->p.proposal == MPV_PROPOSAL_LEARNED;
+    if (learned && !ctx->net.layers) return MPV_ERR_INVALID_ARG;    // no weights loaded
+    mpv_status r = enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t, &ctx->net);
+    if (r == MPV_OK && learned && !dbg) {
+        if (!ctx->edge_host) {
+            if (cudaMallocHost(&ctx->edge_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+                cudaGetLastError();
+                return MPV_ERR_OOM;
+            }
+            ctx->edge_host[0] = ctx->edge_host[1] = 0;
+        }
+        const Layout L = make_layout(g, views_needed(ctx->p, job, dbg), true);
+        cudaMemcpyAsync(ctx->edge_host, (uint8_t *)ctx->ws + L.edge,
+                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        r = cuda_status(cudaGetLastError());
+    }
+    return r;
 }
 
 struct DeviceGuard {
@@ -505,7 +528,106 @@ mpv_status mpv_match_host(mpv_ctx *ctx, const uint8_t *left, const uint8_t *righ
 mpv_status mpv_load_proposal_weights(mpv_ctx *ctx, const char *path)
 {
     if (!ctx || !path) return MPV_ERR_INVALID_ARG;
-    return MPV_ERR_UNSUPPORTED;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return MPV_ERR_INVALID_ARG;
+    std::vector<unsigned char> data;
+    unsigned char buf[65536];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) data.insert(data.end(), buf, buf + got);
+    std::fclose(f);
+    auto rd = [&](size_t off) -> int32_t {
+        int32_t v;
+        std::memcpy(&v, data.data() + off, 4);
+        return v;
+    };
+    if (data.size() < 20 || std::memcmp(data.data(), "MPVP", 4) != 0 || rd(4) != 1 ||
+        rd(8) != kProposalLayers)
+        return MPV_ERR_INVALID_ARG;
+    ProposalNet net;
+    net.layers = kProposalLayers;
+    net.train_D = rd(12);
+    net.factor = rd(16);
+    size_t off = 20, nw = 0, nb = 0;
+    for (int k = 0; k < kProposalLayers; ++k, off += 12) {
+        if (off + 12 > data.size()) return MPV_ERR_INVALID_ARG;
+        net.cin[k] = rd(off);
+        net.cout[k] = rd(off + 4);
+        net.relu[k] = rd(off + 8);
+        const bool lastk = k == kProposalLayers - 1;
+        if (net.cin[k] < 1 || net.cin[k] > 1024 || net.cout[k] != (lastk ? 1 : 32) ||
+            net.relu[k] != (lastk ? 0 : 1) || (k > 0 && net.cin[k] != net.cout[k - 1]))
+            return MPV_ERR_INVALID_ARG;
+        nw += (size_t)net.cout[k] * net.cin[k] * 9;
+        nb += (size_t)net.cout[k];
+    }
+    if (off + 4 * (nw + nb) != data.size()) return MPV_ERR_INVALID_ARG;
+    // device layout: all BF16 weights, then all FP32 biases (256-byte aligned)
+    const size_t wbytes = ((nw * sizeof(__nv_bfloat16)) + 255) & ~(size_t)255;
+    std::vector<__nv_bfloat16> hw(nw);
+    std::vector<float> hb(nb);
+    size_t iw = 0, ib = 0;
+    for (int k = 0; k < kProposalLayers; ++k) {
+        const size_t n = (size_t)net.cout[k] * net.cin[k] * 9;
+        for (size_t i = 0; i < n; ++i, off += 4) {
+            float v;
+            std::memcpy(&v, data.data() + off, 4);
+            hw[iw + i] = __float2bfloat16(v);
+        }
+        std::memcpy(hb.data() + ib, data.data() + off, 4 * (size_t)net.cout[k]);
+        off += 4 * (size_t)net.cout[k];
+        iw += n;
+        ib += net.cout[k];
+    }
+    DeviceGuard guard(ctx->device);
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, wbytes + nb * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return MPV_ERR_OOM;
+    }
+    cudaMemcpy(mem, hw.data(), nw * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
+    cudaMemcpy((uint8_t *)mem + wbytes, hb.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
+    iw = ib = 0;
+    for (int k = 0; k < kProposalLayers; ++k) {
+        net.w[k] = (const __nv_bfloat16 *)mem + iw;
+        net.b[k] = (const float *)((uint8_t *)mem + wbytes) + ib;
+        iw += (size_t)net.cout[k] * net.cin[k] * 9;
+        ib += net.cout[k];
+    }
+    if (ctx->net_mem) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->net_mem);
+    }
+    drop_graphs(ctx);
+    ctx->net_mem = mem;
+    ctx->net = net;
+    return cuda_status(cudaGetLastError());
+}
+
+mpv_status mpv_proposal_features(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                 int32_t width, int32_t height, int32_t pitch, int32_t view,
+                                 void *out, void *cuda_stream)
+{
+    if (!ctx || !left || !right || !out || view < 0 || view > 1) return MPV_ERR_INVALID_ARG;
+    mpv_params p = ctx->p;
+    p.proposal = MPV_PROPOSAL_PYRAMID;
+    const mpv_status v = validate_pair(p, width, height, pitch, width, p.max_disparity);
+    if (v != MPV_OK) return v;
+    DeviceGuard guard(ctx->device);
+    Geometry g;
+    make_geometry(p, width, height, p.max_disparity, g);
+    const mpv_status st = ensure_workspace(ctx, make_layout(g, view == 1 ? 2 : 1).total);
+    if (st != MPV_OK) return st;
+    const PairJob job{left, right, width, height, pitch, p.max_disparity, nullptr, width, nullptr};
+    return enqueue_features(p, job, (uint8_t *)ctx->ws, (cudaStream_t)cuda_stream, view,
+                            (__nv_bfloat16 *)out);
+}
+
+mpv_status mpv_proposal_stats(const mpv_ctx *ctx, uint64_t *edge_hits, uint64_t *pixels)
+{
+    if (!ctx) return MPV_ERR_INVALID_ARG;
+    if (edge_hits) *edge_hits = ctx->edge_host ? ctx->edge_host[0] : 0;
+    if (pixels) *pixels = ctx->edge_host ? ctx->edge_host[1] : 0;
+    return MPV_OK;
 }
 
 mpv_status mpv_sync(mpv_ctx *ctx)
@@ -650,6 +772,8 @@ void mpv_destroy(mpv_ctx *ctx)
             cudaDeviceSynchronize();
             cudaFree(ctx->bws);
         }
+        if (ctx->net_mem) cudaFree(ctx->net_mem);
+        if (ctx->edge_host) cudaFreeHost(ctx->edge_host);
     }
     if (ctx->ws || ctx->stage) {
         DeviceGuard guard(ctx->device);

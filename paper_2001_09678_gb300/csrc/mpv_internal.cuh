@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include "../../include/mpv.h"
 
 namespace mpv {
@@ -45,6 +47,7 @@ struct LevelArgs {
     int radius;      // labels beyond which the truncation dominates: ceil(T/p1) - 1
     int npaths;
     int lanes;       // lanes per scan path for 32/64-label strides (4 or 8; autotuned)
+    unsigned long long *edge;  // optional [2]: WTA at a window edge inside the range, pixels
 };
 
 // Launch shapes chosen per image shape by the autotuner.
@@ -79,6 +82,27 @@ void launch_lr(const uint16_t *dL, const uint16_t *dRm, int W, int H, int tol, i
 // stage dumps: C (u8, stride Dws) -> u16 [.][Dw]; S (u16, stride Dws) -> u32 [.][Dw]
 void launch_unpack(const LevelArgs &a, int view, uint16_t *cost, uint32_t *sum, cudaStream_t s);
 
+// ---- learned proposal ---------------------------------------------------------------------
+
+constexpr int kProposalLayers = 6;
+
+// Device copy of the proposal network (BF16 weights, FP32 biases).
+struct ProposalNet {
+    int layers = 0;
+    int cin[kProposalLayers], cout[kProposalLayers], relu[kProposalLayers];
+    const void *w[kProposalLayers];     // __nv_bfloat16 [cout][cin][3][3]
+    const float *b[kProposalLayers];
+    int train_D = 0, factor = 0;
+};
+
+void launch_conv3x3(const __nv_bfloat16 *in, int N, int Cin, int H, int W, const __nv_bfloat16 *w,
+                    const float *b, int Cout, int relu, __nv_bfloat16 *out_bf, float *out_f,
+                    cudaStream_t s);
+void launch_features(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const uint8_t *C,
+                     int Dws, int Dw, int W, int H, __nv_bfloat16 *out, cudaStream_t s);
+void launch_proposal_windows(const float *q, int Wq, int Hq, int f, int W, int H, int D, int Dw,
+                             uint16_t *lo, cudaStream_t s);
+
 // ---- the pipeline shared by every entry point ----------------------------------------
 
 struct Geometry {
@@ -92,6 +116,8 @@ struct Layout {
     size_t img0[kMaxViews][kMaxScales], img1[kMaxViews][kMaxScales];
     size_t lo[kMaxViews][kMaxScales], d[kMaxViews][kMaxScales];
     size_t C[kMaxViews], S[kMaxViews];
+    size_t feat = 0, act0 = 0, act1 = 0, q = 0;   // learned proposal (both views)
+    size_t edge = 0;                              // edge-hit counters
 };
 
 struct PairJob {
@@ -119,13 +145,18 @@ struct StageSink {
 bool params_valid(const mpv_params &p);
 mpv_status validate_pair(const mpv_params &p, int W, int H, int pitch, int disp_pitch, int D);
 void make_geometry(const mpv_params &p, int W, int H, int D, Geometry &g);
-Layout make_layout(const Geometry &g, int nviews);
+Layout make_layout(const Geometry &g, int nviews, bool learned = false);
+// Window width of the finest level under the learned proposal (centre +- 8 by default).
+int learned_window(const mpv_params &p, int D);
 int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg);
 
 // Enqueues the whole matcher for one pair on stream s, with its scratch at `workspace`
 // (at least make_layout(...).total bytes).
 mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *workspace,
                         cudaStream_t s, const StageHook *hook, const StageSink *dbg,
-                        const Tuning &tune = Tuning());
+                        const Tuning &tune = Tuning(), const ProposalNet *net = nullptr);
+// Network input of the top level of `view` (2 + D_top channels, BF16) into out.
+mpv_status enqueue_features(const mpv_params &p, const PairJob &job, uint8_t *workspace,
+                            cudaStream_t s, int view, __nv_bfloat16 *out);
 
 }  // namespace mpv

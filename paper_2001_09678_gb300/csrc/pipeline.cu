@@ -76,6 +76,8 @@ void make_geometry(const mpv_params &p, int W, int H, int D, Geometry &g)
     if (Dw < 1) Dw = 1;
     for (int l = 0; l < g.S; ++l) {
         g.Dw[l] = l == 0 ? g.D[0] : (Dw < g.D[l] ? Dw : g.D[l]);
+        if (p.proposal == MPV_PROPOSAL_LEARNED && l == g.S - 1 && l > 0)
+            g.Dw[l] = learned_window(p, D);
         g.Dws[l] = (g.Dw[l] + 15) / 16 * 16;
         const int b = l > 0 ? p.block[l - 1] : 0;
         g.block[l] = b > 0 ? b : (l == g.S - 1 ? 1 : 2);
@@ -96,11 +98,17 @@ mpv_status validate_pair(const mpv_params &p, int W, int H, int pitch, int disp_
     const int64_t pen = p.trunc < jump ? p.trunc : jump;
     if ((int64_t)p.num_paths * (255 + pen) >= 65535) return MPV_ERR_INVALID_ARG;
     if ((int64_t)W * H > (int64_t)1 << 27) return MPV_ERR_UNSUPPORTED;
-    if (p.proposal == MPV_PROPOSAL_LEARNED) return MPV_ERR_UNSUPPORTED;
+    if (p.proposal == MPV_PROPOSAL_LEARNED && p.num_scales < 2) return MPV_ERR_INVALID_ARG;
     return MPV_OK;
 }
 
-Layout make_layout(const Geometry &g, int nviews)
+int learned_window(const mpv_params &p, int D)
+{
+    const int w = p.window > 0 ? p.window : 17;
+    return w < D ? w : D;
+}
+
+Layout make_layout(const Geometry &g, int nviews, bool learned)
 {
     Layout L;
     size_t off = 0;
@@ -121,8 +129,42 @@ Layout make_layout(const Geometry &g, int nviews)
         L.C[v] = take(off, sizeof(uint8_t) * (size_t)maxvol);
         L.S[v] = take(off, sizeof(uint16_t) * (size_t)maxvol);
     }
+    if (learned) {
+        const size_t px0 = (size_t)g.W[0] * g.H[0];
+        L.feat = take(off, 2 * sizeof(__nv_bfloat16) * (size_t)(2 + g.Dw[0]) * px0);
+        L.act0 = take(off, 2 * sizeof(__nv_bfloat16) * 32 * px0);
+        L.act1 = take(off, 2 * sizeof(__nv_bfloat16) * 32 * px0);
+        L.q = take(off, 2 * sizeof(float) * px0);
+    }
+    L.edge = take(off, 2 * sizeof(unsigned long long));
     L.total = off;
     return L;
+}
+
+mpv_status enqueue_features(const mpv_params &p, const PairJob &job, uint8_t *base,
+                            cudaStream_t s, int view, __nv_bfloat16 *out)
+{
+    mpv_params q = p;
+    q.proposal = MPV_PROPOSAL_PYRAMID;
+    q.lr_check = view == 1 ? 1 : 0;
+    Geometry g;
+    make_geometry(q, job.W, job.H, job.D, g);
+    const int nviews = view == 1 ? 2 : 1;
+    const Layout L = make_layout(g, nviews);
+    // run the top level's cost (a debug stage of level 0), then build the features
+    StageSink dbg;
+    dbg.view = view;
+    dbg.level = 0;
+    const mpv_status st = enqueue_pair(q, job, base, s, nullptr, &dbg);
+    if (st != MPV_OK) return st;
+    const int top = g.S - 1;
+    const uint8_t *I0 = (view == 0 && top == 0) ? job.left : base + L.img0[view][0];
+    const uint8_t *I1 = (view == 0 && top == 0) ? job.right : base + L.img1[view][0];
+    const int pitch = (view == 0 && top == 0) ? job.pitch : g.pitch[0];
+    launch_features(I0, pitch, I1, pitch, base + L.C[view], g.Dws[0], g.Dw[0], g.W[0], g.H[0],
+                    out, s);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPV_OK : MPV_ERR_CUDA;
 }
 
 int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg)
@@ -131,12 +173,20 @@ int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg)
 }
 
 mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, cudaStream_t s,
-                        const StageHook *hook, const StageSink *dbg, const Tuning &tune)
+                        const StageHook *hook, const StageSink *dbg, const Tuning &tune,
+                        const ProposalNet *net)
 {
     Geometry g;
     make_geometry(p, job.W, job.H, job.D, g);
     const int nviews = views_needed(p, job, dbg);
-    const Layout L = make_layout(g, nviews);
+    const bool learned = p.proposal == MPV_PROPOSAL_LEARNED;
+    if (learned) {
+        if (!net || net->layers != kProposalLayers || net->cin[0] != 2 + g.Dw[0] || g.S < 2)
+            return MPV_ERR_INVALID_ARG;
+        if (dbg && dbg->level != 0 && dbg->level != g.S - 1) return MPV_ERR_INVALID_ARG;
+    }
+    const Layout L = make_layout(g, nviews, learned);
+    unsigned long long *edge = (unsigned long long *)(base + L.edge);
     const int S = g.S;
     const int top = S - 1;
 
@@ -172,7 +222,9 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
     }
 
     const int last = dbg ? dbg->level : top;
+    if (!dbg) cudaMemsetAsync(edge, 0, 2 * sizeof(unsigned long long), s);
     for (int l = 0; l <= last; ++l) {
+        if (learned && l > 0 && l < top) continue;
         LevelArgs a{};
         a.W = g.W[l];
         a.H = g.H[l];
@@ -203,7 +255,16 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             vl.S = (uint16_t *)(base + L.S[v]);
             vl.d = (uint16_t *)(base + L.d[v][l]);
         }
-        if (l > 0) {
+        a.edge = (learned && l == top) ? edge : nullptr;
+        if (learned && l == top) {
+            // windows of the finest level from the network's prediction at the top level
+            HookScope hs(hook, MPV_STAGE_SEED, nviews, s);
+            const float *q = (const float *)(base + L.q);
+            const size_t px0 = (size_t)g.W[0] * g.H[0];
+            for (int v = 0; v < nviews; ++v)
+                launch_proposal_windows(q + v * px0, g.W[0], g.H[0], 1 << (g.S - 1), a.W, a.H,
+                                        a.D, a.Dw, (uint16_t *)(base + L.lo[v][l]), s);
+        } else if (l > 0) {
             HookScope hs(hook, MPV_STAGE_SEED, 1, s);
             SeedArgs sa{};
             sa.W = g.W[l];
@@ -223,6 +284,27 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
         {
             HookScope hs(hook, MPV_STAGE_COST, 1, s);
             launch_cost(a, s);
+        }
+        if (learned && l == 0) {
+            HookScope hs(hook, MPV_STAGE_SEED, 2 + net->layers, s);
+            const size_t px0 = (size_t)a.W * a.H;
+            const int cin0 = 2 + a.Dw;
+            __nv_bfloat16 *feat = (__nv_bfloat16 *)(base + L.feat);
+            for (int v = 0; v < nviews; ++v)
+                launch_features(a.v[v].I0, a.v[v].pitch0, a.v[v].I1, a.v[v].pitch1, a.v[v].C,
+                                a.Dws, a.Dw, a.W, a.H, feat + v * cin0 * px0, s);
+            const __nv_bfloat16 *in = feat;
+            __nv_bfloat16 *bufs[2] = {(__nv_bfloat16 *)(base + L.act0),
+                                      (__nv_bfloat16 *)(base + L.act1)};
+            for (int k = 0; k < net->layers; ++k) {
+                const bool lastk = k + 1 == net->layers;
+                launch_conv3x3(in, nviews, net->cin[k], a.H, a.W,
+                               (const __nv_bfloat16 *)net->w[k], net->b[k], net->cout[k],
+                               net->relu[k], lastk ? nullptr : bufs[k & 1],
+                               lastk ? (float *)(base + L.q) : nullptr, s);
+                in = bufs[k & 1];
+            }
+            if (!(dbg && dbg->level == 0)) continue;
         }
         {
             HookScope hs(hook, MPV_STAGE_AGGREGATE, 1, s);

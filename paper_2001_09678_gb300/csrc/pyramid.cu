@@ -106,7 +106,20 @@ __global__ void wta_kernel(LevelArgs a)
     }
     best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 1));
     best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 2));
-    if (in && sub == 0) v.d[i] = (uint16_t)((v.lo ? v.lo[i] : 0) + (best & 0xFFFFu));
+    const int lo = (in && v.lo) ? (int)v.lo[i] : 0;
+    if (in && sub == 0) v.d[i] = (uint16_t)(lo + (best & 0xFFFFu));
+    if (a.edge) {
+        // the minimum sits on the window's edge while the range continues beyond it
+        const int k = (int)(best & 0xFFFFu);
+        const bool hit = in && sub == 0 &&
+                         ((k == 0 && lo > 0) || (k == a.Dw - 1 && lo + a.Dw < a.D));
+        const unsigned nh = __popc(__ballot_sync(0xFFFFFFFFu, hit));
+        const unsigned np = __popc(__ballot_sync(0xFFFFFFFFu, in && sub == 0));
+        if ((threadIdx.x & 31) == 0 && np) {
+            atomicAdd(a.edge, (unsigned long long)nh);
+            atomicAdd(a.edge + 1, (unsigned long long)np);
+        }
+    }
 }
 
 // Stage dump: C and S in the documented [H][W][Dw] layout (u16 and u32).

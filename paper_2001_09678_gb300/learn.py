@@ -162,3 +162,202 @@ class Net:
         grads = self.backward(acts, grad)
         self.adam(grads, lr)
         return loss
+
+
+# ---------------------------------------------------------------------------------------
+# Training and evaluation
+# ---------------------------------------------------------------------------------------
+
+W_TRAIN, H_TRAIN, D_TRAIN, S_TRAIN = 1280, 720, 128, 3
+BASE = dict(max_disparity=D_TRAIN, num_scales=S_TRAIN, num_paths=8, p1=10, trunc=30)
+
+
+def _gen_pair(seed):
+    from . import synth
+    L, R, _ = synth.slanted_pair(W_TRAIN, H_TRAIN, seed=seed)
+    return seed, L, R
+
+
+def _constant_layers(cin0, value):
+    layers = init_weights(cin0, seed=0)
+    out = []
+    for i, (w, b, relu) in enumerate(layers):
+        w = np.zeros_like(w)
+        b = np.zeros_like(b)
+        if i == len(layers) - 1:
+            b[:] = value
+        out.append((w, b, relu))
+    return out
+
+
+class _Samples:
+    """Features and targets of both views of each pair, produced by the library."""
+
+    def __init__(self, torch):
+        self.torch = torch
+        f = 1 << (S_TRAIN - 1)
+        self.Wq, self.Hq = (W_TRAIN + f - 1) // f, (H_TRAIN + f - 1) // f
+        self.cin = 2 + (D_TRAIN + f - 1) // f
+        self.ctx = mpv.mpv_create(0)
+        mpv.mpv_set_params(self.ctx, mpv.mpv_default_params(lr_check=0, **BASE))
+        self.disp = torch.empty((H_TRAIN, W_TRAIN), dtype=torch.int16, device="cuda")
+        self.disp_r = torch.empty((H_TRAIN, W_TRAIN), dtype=torch.int16, device="cuda")
+
+    def make(self, L, R, feats_out, targets_out):
+        """Writes 2 samples (left view, mirrored right view) into the given slots."""
+        torch = self.torch
+        l, r = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+        mpv.mpv_proposal_features(self.ctx, l, r, 0, feats_out[0])
+        mpv.mpv_proposal_features(self.ctx, l, r, 1, feats_out[1])
+        mpv.mpv_match_batch(self.ctx, [dict(left=l, right=r, disp=self.disp,
+                                            disp_right=self.disp_r)])
+        f = 1 << (S_TRAIN - 1)
+        mpv.mpv_cnn_target(self.disp, f, D_TRAIN, targets_out[0])
+        # the right view's map in the mirrored problem's coordinates
+        mirrored = torch.flip(self.disp_r, dims=[1]).contiguous()
+        mpv.mpv_cnn_target(mirrored, f, D_TRAIN, targets_out[1])
+
+    def close(self):
+        mpv.mpv_destroy(self.ctx)
+
+
+def train(seconds=600.0, out="proposal.bin", capacity=4096, batch=8, steps_per_pair=4,
+          lr=1e-3, delta=1.0 / 128, seed0=10000, log=print):
+    import multiprocessing as mp
+    import os
+    import time
+
+    import torch
+    mpv.load()
+    smp = _Samples(torch)
+    feats = torch.empty((capacity, smp.cin, smp.Hq, smp.Wq), dtype=torch.bfloat16, device="cuda")
+    targets = torch.empty((capacity, 1, smp.Hq, smp.Wq), dtype=torch.float32, device="cuda")
+    net = Net(init_weights(smp.cin, seed=1))
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    n = 0
+    pairs = 0
+    t0 = time.perf_counter()
+    losses = []
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        for _seed, L, R in pool.imap_unordered(_gen_pair, range(seed0, seed0 + 10**6), 4):
+            slot = n % capacity
+            s2 = (slot + 1) % capacity
+            smp.make(L, R, (feats[slot], feats[s2]), (targets[slot], targets[s2]))
+            n += 2
+            pairs += 1
+            have = min(n, capacity)
+            for _ in range(steps_per_pair):
+                idx = torch.randint(0, have, (batch,), generator=gen).cuda()
+                frac = min(1.0, (time.perf_counter() - t0) / seconds)
+                step_lr = lr * (0.1 ** frac)
+                loss = net.train_step(feats[idx].contiguous(), targets[idx].contiguous(),
+                                      step_lr, delta)
+            if pairs % 50 == 0:
+                losses.append(float(loss.item()))
+                log(f"pairs {pairs} samples {n} loss {losses[-1]:.5f} "
+                    f"t {time.perf_counter() - t0:.0f}s")
+            if time.perf_counter() - t0 > seconds:
+                pool.terminate()
+                break
+    smp.close()
+    save_weights(out, net.numpy_layers(), D_TRAIN, 1 << (S_TRAIN - 1))
+    return dict(pairs=pairs, samples=n, steps=net.step, losses=losses,
+                seconds=time.perf_counter() - t0)
+
+
+def evaluate(weights, npairs=40, seed0=900000, log=print):
+    """Bad-pixel rate (> 1 px) against full-range single-scale MPV of: the pyramid, the
+    trained proposal, an untrained network and a constant-centre network; edge-hit rate
+    and frame time of each."""
+    import multiprocessing as mp
+    import os
+    import tempfile
+    import time
+
+    import torch
+    mpv.load()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        data = pool.map(_gen_pair, range(seed0, seed0 + npairs))
+    f = 1 << (S_TRAIN - 1)
+    cin = 2 + (D_TRAIN + f - 1) // f
+    tmp = tempfile.mkdtemp()
+    variants = {"trained": weights}
+    for name, layers in (("untrained", init_weights(cin, seed=7)),
+                         ("constant", _constant_layers(cin, 0.5))):
+        p = os.path.join(tmp, name + ".bin")
+        save_weights(p, layers, D_TRAIN, f)
+        variants[name] = p
+
+    def ctx_for(**kw):
+        c = mpv.mpv_create(0)
+        prm = dict(BASE)
+        prm.update(kw)
+        mpv.mpv_set_params(c, mpv.mpv_default_params(**prm))
+        return c
+
+    full = ctx_for(num_scales=1)
+    pyr = ctx_for()
+    learned = {}
+    for name, p in variants.items():
+        c = ctx_for(proposal=mpv.MPV_PROPOSAL_LEARNED)
+        mpv.mpv_load_proposal_weights(c, p)
+        learned[name] = c
+    stats = {k: dict(bad=0, both=0, edge=0, px=0, ms=0.0, fallback=0)
+             for k in ["pyramid"] + list(variants)}
+    d_ref = torch.empty((H_TRAIN, W_TRAIN), dtype=torch.int16, device="cuda")
+    d = torch.empty_like(d_ref)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _seed, L, R in data:
+        l, r = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+        mpv.mpv_match(full, l, r, d_ref)
+        ref_np = d_ref.cpu().numpy().view(np.uint16)
+        for name, c in [("pyramid", pyr)] + list(learned.items()):
+            for _ in range(2):           # the second run is timed (warm workspace)
+                ev0.record()
+                mpv.mpv_match(c, l, r, d)
+                ev1.record()
+            torch.cuda.synchronize()
+            st = stats[name]
+            st["ms"] += ev0.elapsed_time(ev1)
+            got = d.cpu().numpy().view(np.uint16)
+            both = (got != 0xFFFF) & (ref_np != 0xFFFF)
+            st["both"] += int(both.sum())
+            st["bad"] += int((np.abs(got.astype(int) - ref_np.astype(int)) > 1)[both].sum())
+            if name != "pyramid":
+                hits, px = mpv.mpv_proposal_stats(c)
+                st["edge"] += hits
+                st["px"] += px
+    for c in [full, pyr] + list(learned.values()):
+        mpv.mpv_destroy(c)
+    out = {}
+    for k, st in stats.items():
+        out[k] = dict(bad_pixel_rate=st["bad"] / max(1, st["both"]),
+                      edge_hit_rate=(st["edge"] / st["px"]) if st["px"] else None,
+                      ms_per_frame=st["ms"] / npairs)
+        log(f"{k:10s} bad>1px {out[k]['bad_pixel_rate']:.4f}  edge {out[k]['edge_hit_rate']}  "
+            f"{out[k]['ms_per_frame']:.3f} ms")
+    return out
+
+
+def main():
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--seconds", type=float, default=600.0)
+    ap.add_argument("--out", default="proposal.bin")
+    ap.add_argument("--eval-pairs", type=int, default=40)
+    ap.add_argument("--eval-only", action="store_true")
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args()
+    res = {}
+    if not args.eval_only:
+        res["train"] = train(seconds=args.seconds, out=args.out)
+    res["eval"] = evaluate(args.out, npairs=args.eval_pairs)
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump(res, f, indent=1)
+    print(json.dumps(res["eval"]))
+
+
+if __name__ == "__main__":
+    main()

@@ -85,7 +85,7 @@ EXPORTS = [
     "mpv_server_submit", "mpv_server_poll", "mpv_server_stats", "mpv_server_destroy",
     "mpv_cnn_conv3x3", "mpv_cnn_conv3x3_wgrad", "mpv_cnn_flip_transpose",
     "mpv_cnn_relu_backward", "mpv_cnn_huber", "mpv_cnn_adam", "mpv_cnn_to_bf16",
-    "mpv_cnn_target",
+    "mpv_cnn_target", "mpv_proposal_features", "mpv_proposal_stats",
 ]
 MPV_NOALLOC_SCRATCH_BYTES = 64 << 20
 MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
@@ -140,6 +140,8 @@ def load(path: str = LIB_PATH):
                                i32, vp, vp]
     L.mpv_cnn_to_bf16.argtypes = [vp, vp, i64, vp]
     L.mpv_cnn_target.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp]
+    L.mpv_proposal_features.argtypes = [ctx, vp, vp, i32, i32, i32, i32, vp, vp]
+    L.mpv_proposal_stats.argtypes = [ctx, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     L.mpv_destroy.argtypes = [ctx]
     L.mpv_destroy.restype = None
     L.mpv_server_destroy.restype = None
@@ -401,6 +403,20 @@ def mpv_cnn_target(disp, factor, max_disparity, target, stream=None):
     H, W = disp.shape[-2], disp.shape[-1]
     _check(load().mpv_cnn_target(_ptr(disp), disp.stride(-2), W, H, factor, max_disparity,
                                  _ptr(target), _stream(stream)), "mpv_cnn_target")
+
+
+def mpv_proposal_features(ctx, left, right, view, out, stream=None):
+    H, W = left.shape[-2], left.shape[-1]
+    _check(load().mpv_proposal_features(ctx, _ptr(left), _ptr(right), W, H, left.stride(-2),
+                                        view, _ptr(out), _stream(stream)),
+           "mpv_proposal_features")
+
+
+def mpv_proposal_stats(ctx):
+    """(edge hits, pixels) of the last learned-proposal match (after mpv_sync)."""
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(load().mpv_proposal_stats(ctx, C.byref(a), C.byref(b)), "mpv_proposal_stats")
+    return a.value, b.value
 
 
 def mpv_destroy(ctx) -> None:
