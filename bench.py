@@ -32,7 +32,7 @@ METRIC = "Mdisp-evals/s at 1280x720 D=128 (3-scale MPV, 8 paths, left-right chec
 UNIT = "Mdisp-evals/s"
 WORKLOAD = ("1280x720 uint8 pair, D=128, 3 scales (factor 2, windows D/4), 8 paths, "
             "p1=10, T=30, N=5, left-right check")
-CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 L2_FLUSH_BYTES = 256 << 20
@@ -69,17 +69,17 @@ def level_geometry():
 
 
 def algorithmic_bytes(views=2):
-    """Minimum HBM bytes per frame of each stage: the cost kernel writes the uint16
-    cost volume (2 B/node) after reading both images; the aggregation reads it (2 B/node)
-    and writes the uint16 summed volume (2 B/node); winner-take-all reads that (2 B/node)
-    and writes the uint16 map."""
+    """Minimum HBM bytes per frame of each stage: the cost kernel reads both images and
+    writes the cost volume (1 B/node: costs are <= 255); the aggregation reads it
+    (1 B/node) and writes the uint16 summed volume (2 B/node); winner-take-all reads
+    that (2 B/node) and writes the uint16 map."""
     cost = agg = wta = 0
     nodes = 0
     for (w, h, Dl, Dw) in level_geometry():
         n = w * h * Dw
         nodes += n
-        cost += views * (2 * n + 2 * w * h)
-        agg += views * (2 * n + 2 * n + 2 * w * h)
+        cost += views * (n + 2 * w * h)
+        agg += views * (n + 2 * n + 2 * w * h)
         wta += views * (2 * n + 2 * w * h + 2 * w * h)
     return dict(cost=cost, aggregate=agg, wta=wta), nodes
 
@@ -98,7 +98,7 @@ class ClockSampler:
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -114,18 +114,27 @@ class ClockSampler:
                 self.p.kill()
         self.f.flush()
 
+    def mark(self, start, end):
+        """Wall-clock window (time.time()) of the timed region."""
+        self.window = (start, end)
+
     def summary(self):
+        import datetime
         self.f.seek(0)
         rows = [ln.strip().split(",") for ln in self.f if ln.strip()]
         os.unlink(self.f.name)
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        win = getattr(self, "window", None)
         for r in rows:
             try:
                 r = [x.strip() for x in r]
-                sm.append(float(r[1]))
-                smax = max(smax, float(r[2]))
-                for nm, v in zip(names, r[5:9]):
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if win and not (win[0] - 0.06 <= ts <= win[1] + 0.06):
+                    continue
+                sm.append(float(r[2]))
+                smax = max(smax, float(r[3]))
+                for nm, v in zip(names, r[6:10]):
                     if v.lower().startswith("active"):
                         reasons.add(nm)
             except (ValueError, IndexError):
@@ -191,6 +200,7 @@ def run_mine(args):
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        w0 = time.time()
         for i in range(args.steps):
             flush.fill_(i & 0xFF)          # L2 flush between timed steps (not timed)
             starts[i].record(stream)
@@ -199,6 +209,7 @@ def run_mine(args):
         torch.cuda.synchronize(dev)
         barrier()
         wall = time.perf_counter() - t0
+        clocks.mark(w0, time.time())
     prof = mpv.mpv_profile_read(ctx)
     mpv.mpv_profile_enable(ctx, False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -316,7 +327,10 @@ def run_reference(args):
     from oracle import ref
     from paper_2001_09678_gb300 import synth
     L, R, _ = synth.slanted_pair(W, H, seed=0)
-    rows = 90                      # bounded sample: a 1280x90 strip through the matcher
+    # bounded sample: a 1280 x rows strip through the matcher, sized so that the whole
+    # run (warm-up + steps) takes about two minutes; at least 20 rows keep the top level
+    # of the 3-scale pyramid >= 5 rows high
+    rows = int(min(180, max(20, 8000 // max(1, args.steps + args.warmup))))
     y0 = (H - rows) // 2
     Ls, Rs = L[y0:y0 + rows].copy(), R[y0:y0 + rows].copy()
     p = _ora_params()
@@ -402,8 +416,8 @@ def _gen_pair(spec):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("mine", "reference"), default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=("frame", "batch64"), default="frame",

@@ -226,6 +226,114 @@ __global__ void proposal_windows_kernel(const float *__restrict__ q, int Wq, int
     lo[(int64_t)y * W + x] = (uint16_t)min(max(l, 0), D - Dw);
 }
 
+
+// Tensor-core form of conv3x3_kernel<32, bf16> (inference and training forward): an
+// implicit GEMM  out[p][co] = sum_k A[p][k] B[k][co]  with p = pixel, k = (tap, ci).
+// The block stages its input tile channels-last in shared memory (channel stride CP,
+// padded so that ldmatrix rows fall in distinct banks) and the weights as [co][tap][ci],
+// then every warp multiplies 32 pixels x 32 channels with mma.sync m16n8k16 (BF16 in,
+// FP32 accumulate).  Tile: 8 rows x 16 columns of pixels, 4 warps of 2 rows each.
+constexpr int kMmaRows = 8, kMmaCols = 16;
+
+__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
+                                        const void *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned &r0, unsigned &r1, const void *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r0), "=r"(r1) : "r"(a));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128) conv3x3_mma_kernel(
+    const __nv_bfloat16 *__restrict__ in, int Cin, int CP, int H, int W,
+    const __nv_bfloat16 *__restrict__ w, const float *__restrict__ b, int relu,
+    __nv_bfloat16 *__restrict__ out_bf, float *__restrict__ out_f)
+{
+    extern __shared__ __align__(16) __nv_bfloat16 sm[];
+    constexpr int TR = kMmaRows + 2, TC = kMmaCols + 2;
+    __nv_bfloat16 *xs = sm;                              // [TR][TC][CP]
+    __nv_bfloat16 *ws = sm + TR * TC * CP;               // [32][9][CP]
+    const int n = blockIdx.z;
+    const int x0 = blockIdx.x * kMmaCols, y0 = blockIdx.y * kMmaRows;
+    const int64_t plane = (int64_t)H * W;
+    const __nv_bfloat16 *src = in + (int64_t)n * Cin * plane;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    // consecutive threads read consecutive pixels (input) and taps (weights)
+    for (int i = threadIdx.x; i < TR * TC * CP; i += 128) {
+        const int px = i % TC, q = i / TC, py = q % TR, c = q / TR;
+        const int yy = y0 - 1 + py, xx = x0 - 1 + px;
+        xs[(py * TC + px) * CP + c] = (c < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                                          ? src[c * plane + (int64_t)yy * W + xx] : zero;
+    }
+    for (int i = threadIdx.x; i < 32 * 9 * CP; i += 128) {
+        const int tap = i % 9, q = i / 9, c = q % CP, co = q / CP;
+        ws[(co * 9 + tap) * CP + c] = c < Cin ? w[((int64_t)co * Cin + c) * 9 + tap] : zero;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    // ldmatrix row addresses: A rows = pixels of row (2*warp + mt), B rows = channels
+    const int arow = lane & 15, acol = (lane >> 4) * 8;
+    const int brow = lane & 7, bcol = ((lane >> 3) & 1) * 8;
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        for (int c0 = 0; c0 < CP - 8; c0 += 16) {
+            unsigned a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int py = 2 * warp + mt + ky, px = arow + kx;
+                ldsm_x4(a[mt][0], a[mt][1], a[mt][2], a[mt][3], xs + (py * TC + px) * CP + c0 + acol);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                unsigned b0, b1;
+                ldsm_x2(b0, b1, ws + ((nt * 8 + brow) * 9 + tap) * CP + c0 + bcol);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+                    mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+            }
+        }
+    }
+    // accumulator layout: d0,d1 at (row g, cols 2t, 2t+1), d2,d3 at (row g+8, same cols)
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int y = y0 + 2 * warp + mt;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int x = x0 + g + (e >= 2 ? 8 : 0);
+                const int co = nt * 8 + 2 * t + (e & 1);
+                if (x >= W || y >= H) continue;
+                float v = acc[mt][nt][e] + (b ? b[co] : 0.f);
+                if (relu) v = fmaxf(v, 0.f);
+                const int64_t o = ((int64_t)n * 32 + co) * plane + (int64_t)y * W + x;
+                if (out_f) out_f[o] = v;
+                if (out_bf) out_bf[o] = __float2bfloat16(v);
+            }
+    }
+}
+
 unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -252,7 +360,16 @@ void launch_conv3x3(const __nv_bfloat16 *in, int N, int Cin, int H, int W, const
                     const float *b, int Cout, int relu, __nv_bfloat16 *out_bf, float *out_f,
                     cudaStream_t s)
 {
-    launch_conv3x3_t(in, N, Cin, H, W, w, b, Cout, relu, out_bf, out_f, s);
+    if (Cout != 32) {
+        launch_conv3x3_t(in, N, Cin, H, W, w, b, Cout, relu, out_bf, out_f, s);
+        return;
+    }
+    // channel stride: Cin rounded up to 16 (whole k-steps) plus 8 (bank spread)
+    const int CP = (Cin + 15) / 16 * 16 + 8;
+    const size_t smem = sizeof(__nv_bfloat16) * (size_t)CP * ((kMmaRows + 2) * (kMmaCols + 2) + 32 * 9);
+    dim3 grid((W + kMmaCols - 1) / kMmaCols, (H + kMmaRows - 1) / kMmaRows, N);
+    cudaFuncSetAttribute(conv3x3_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    conv3x3_mma_kernel<<<grid, 128, smem, s>>>(in, Cin, CP, H, W, w, b, relu, out_bf, out_f);
 }
 
 void launch_conv3x3_wgrad(const __nv_bfloat16 *in, int N, int Cin, const float *g, int Cout, int H,
