@@ -145,6 +145,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(value, world, device=None):
+    """Max of a per-rank float over all ranks (identity on one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_step, steps, world, slowest_ms):
+    """Whole-job Mdisp-evals/s: every rank matched `steps` pairs; time of the slowest."""
+    return world * steps * units_per_step / (slowest_ms / 1e3) / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -213,14 +229,9 @@ def run_mine(args):
     prof = mpv.mpv_profile_read(ctx)
     mpv.mpv_profile_enable(ctx, False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps * nominal_units() / (total_ms / 1e3) / 1e6
+    value = replica_throughput(nominal_units(), args.steps, world, total_ms)
 
     # end to end through the host entry point: pinned host buffers, copies inside
     hl = torch.from_numpy(L).pin_memory()
@@ -236,13 +247,8 @@ def run_mine(args):
         t1 = time.perf_counter()
         mpv.mpv_match_host(ctx, hl, hr, hd, stream)   # synchronizes before returning
         e2e_times.append(time.perf_counter() - t1)
-    e2e_s = sum(e2e_times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * args.steps * nominal_units() / e2e_s / 1e6
+    e2e_s = reduce_max(sum(e2e_times), world, dev)
+    e2e_value = replica_throughput(nominal_units(), args.steps, world, 1e3 * e2e_s)
     ok = np.array_equal(hd.numpy(), disp.cpu().numpy())
 
     # roofline of the dominant kernel (by device time over the timed region)
