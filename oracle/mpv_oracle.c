@@ -244,6 +244,227 @@ int ora_aggregate(const int32_t *C, const int32_t *lo, int W, int H, int Dw, int
     return status;
 }
 
+/* ------------------------------------------------------------------------------ */
+/* Penalties per step: the gradient-weighted TV term and the paper's asymmetric     */
+/* left-to-right pass; the hierarchical merge of Section 3.2                         */
+/* ------------------------------------------------------------------------------ */
+
+static int64_t eps_pen(int64_t u, int64_t v, const ora_penalty *e)
+{
+    if (u == v) return 0;
+    const int64_t up = u > v;
+    const int64_t d = up ? u - v : v - u;
+    const int64_t slope = up ? e->p_up : e->p_dn;
+    const int64_t T = up ? e->T_up : e->T_dn;
+    const int64_t x = slope * d;
+    return (T >= ORA_NO_TRUNC) ? x : min64(x, T);
+}
+
+/* Full connectivity with the step's penalty: O(Dw^2). */
+void ora_envelope_naive_pen(const int64_t *A, int lo_prev, int lo, int Dw,
+                            const ora_penalty *e, int64_t *M)
+{
+    for (int k = 0; k < Dw; ++k) {
+        int64_t best = ORA_INF;
+        for (int j = 0; j < Dw; ++j)
+            best = min64(best, A[j] + eps_pen(lo + k, lo_prev + j, e));
+        M[k] = best;
+    }
+}
+
+/* Section 3.3 with two slopes: predecessors v <= u are reached by the upward sweep
+ *     F(u) = min(A(u), F(u-1) + p_up),
+ * predecessors v >= u by the downward sweep
+ *     G(u) = min(A(u), G(u+1) + p_dn),
+ * and the truncations by the running minima of A from each side:
+ *     M'(u) = min(F(u), G(u), min_{v<=u} A(v) + T_up, min_{v>=u} A(v) + T_dn).
+ * With p_up = p_dn and T_up = T_dn this is the symmetric envelope of ora_envelope_fast. */
+void ora_envelope_fast_pen(const int64_t *A, int lo_prev, int lo, int Dw,
+                           const ora_penalty *e, int64_t *M)
+{
+    const int ulo = lo < lo_prev ? lo : lo_prev;
+    const int uhi = (lo > lo_prev ? lo : lo_prev) + Dw;  /* exclusive */
+    const int n = uhi - ulo;
+    int64_t *F = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *G = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *P = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *Sm = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t run = ORA_INF, pm = ORA_INF;
+    for (int i = 0; i < n; ++i) {
+        const int u = ulo + i;
+        const int64_t a = (u >= lo_prev && u < lo_prev + Dw) ? A[u - lo_prev] : ORA_INF;
+        run = min64(a, run + e->p_up);
+        if (run > ORA_INF) run = ORA_INF;
+        pm = min64(pm, a);
+        F[i] = run;
+        P[i] = pm;
+    }
+    run = ORA_INF;
+    pm = ORA_INF;
+    for (int i = n - 1; i >= 0; --i) {
+        const int u = ulo + i;
+        const int64_t a = (u >= lo_prev && u < lo_prev + Dw) ? A[u - lo_prev] : ORA_INF;
+        run = min64(a, run + e->p_dn);
+        if (run > ORA_INF) run = ORA_INF;
+        pm = min64(pm, a);
+        G[i] = run;
+        Sm[i] = pm;
+    }
+    for (int k = 0; k < Dw; ++k) {
+        const int i = lo + k - ulo;
+        int64_t m = min64(F[i], G[i]);
+        if (e->T_up < ORA_NO_TRUNC) m = min64(m, P[i] + e->T_up);
+        if (e->T_dn < ORA_NO_TRUNC) m = min64(m, Sm[i] + e->T_dn);
+        M[k] = m;
+    }
+    free(F);
+    free(G);
+    free(P);
+    free(Sm);
+}
+
+/* Slope of the step into pixel (x,y) from its predecessor (px,py): Eq. EU weights the
+ * TV term by e^{-|G|}, G the intensity gradient of I0; here G is the intensity
+ * difference between the two pixels the step connects, and the weight comes from a
+ * caller-supplied table of 256 integer slopes (f2 reading: the table replaces
+ * lambda e^{-|G|} and keeps the penalty an integer).                                  */
+static int64_t step_slope(int64_t p1, const int32_t *lut, const uint8_t *I0, int pitch, int x,
+                          int y, int px, int py)
+{
+    if (!lut) return p1;
+    const int a = I0[(int64_t)y * pitch + x], b = I0[(int64_t)py * pitch + px];
+    return lut[a > b ? a - b : b - a];
+}
+
+int ora_path_pen(const int64_t *Q, const int32_t *lo, int W, int H, int Dw, int dx, int dy,
+                 int64_t p1, int64_t T, const int32_t *lut, const uint8_t *I0, int pitch,
+                 int double_up, int normalize_out, int use_naive, int check, int64_t *L)
+{
+    int status = 0;
+    int64_t *M = (int64_t *)malloc(sizeof(int64_t) * (size_t)Dw);
+    int64_t *M2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)Dw);
+    /* the bounded energies of the predecessor are kept apart from the output, which
+     * may be normalised                                                              */
+    int64_t *B = (int64_t *)malloc(sizeof(int64_t) * (size_t)W * H * Dw);
+    for (int yi = 0; yi < H; ++yi) {
+        const int y = dy >= 0 ? yi : H - 1 - yi;
+        for (int xi = 0; xi < W; ++xi) {
+            const int x = dx >= 0 ? xi : W - 1 - xi;
+            const int64_t idx = (int64_t)y * W + x;
+            const int64_t *q = Q + idx * Dw;
+            int64_t *b = B + idx * Dw;
+            const int px = x - dx, py = y - dy;
+            if (px < 0 || px >= W || py < 0 || py >= H) {
+                for (int k = 0; k < Dw; ++k) b[k] = q[k];
+            } else {
+                const int64_t pidx = (int64_t)py * W + px;
+                const int64_t *A = B + pidx * Dw;
+                const int lo_p = lo ? lo[idx] : 0;
+                const int lo_q = lo ? lo[pidx] : 0;
+                const int64_t P = step_slope(p1, lut, I0, pitch, x, y, px, py);
+                ora_penalty e;
+                e.p_dn = P;
+                e.T_dn = T;
+                e.p_up = double_up ? 2 * P : P;
+                e.T_up = (double_up && T < ORA_NO_TRUNC) ? 2 * T : T;
+                if (use_naive)
+                    ora_envelope_naive_pen(A, lo_q, lo_p, Dw, &e, M);
+                else
+                    ora_envelope_fast_pen(A, lo_q, lo_p, Dw, &e, M);
+                if (check) {
+                    if (use_naive)
+                        ora_envelope_fast_pen(A, lo_q, lo_p, Dw, &e, M2);
+                    else
+                        ora_envelope_naive_pen(A, lo_q, lo_p, Dw, &e, M2);
+                    for (int k = 0; k < Dw; ++k)
+                        if (M[k] != M2[k]) status = -1;
+                }
+                int64_t amin = ORA_INF;
+                for (int j = 0; j < Dw; ++j) amin = min64(amin, A[j]);
+                for (int k = 0; k < Dw; ++k) b[k] = q[k] + M[k] - amin;
+            }
+            int64_t bmin = ORA_INF;
+            for (int k = 0; k < Dw; ++k) bmin = min64(bmin, b[k]);
+            int64_t *l = L + idx * Dw;
+            for (int k = 0; k < Dw; ++k) l[k] = b[k] - (normalize_out ? bmin : 0);
+        }
+    }
+    free(B);
+    free(M);
+    free(M2);
+    return status;
+}
+
+int ora_aggregate_grad(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                       int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                       const uint8_t *I0, int pitch, int64_t *S)
+{
+    const int64_t n = (int64_t)W * H * Dw;
+    int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *L = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!Q || !L) {
+        free(Q);
+        free(L);
+        return -2;
+    }
+    for (int64_t i = 0; i < n; ++i) Q[i] = C[i];
+    memset(S, 0, sizeof(int64_t) * (size_t)n);
+    int status = 0;
+    for (int r = 0; r < num_paths; ++r) {
+        if (ora_path_pen(Q, lo, W, H, Dw, ora_dirs[r][0], ora_dirs[r][1], p1, T, lut, I0, pitch,
+                         0, 0, 0, 0, L))
+            status = -1;
+        for (int64_t i = 0; i < n; ++i) S[i] += L[i];
+    }
+    free(Q);
+    free(L);
+    return status;
+}
+
+/* Section 3.2, Fig. merging and Table alg: the passes run in layers - left/right,
+ * up/down, then the two diagonal pairs - each layer a forward and a backward pass over
+ * the previous layer's node energies (the cost for the first layer).  The two passes
+ * of a layer are compared after per-pixel min-normalisation (reading: the paper gives
+ * no scale for the energies it merges), and merged by the minimum for the horizontal
+ * layer (sharper edges) and by the mean, rounded down, for the others (less noise).
+ * The left-to-right pass charges a jump from a smaller to a larger disparity twice
+ * (reading: "twice penalty" doubles both the slope and the truncation).  The last
+ * layer's merged energies are the output.                                            */
+int ora_aggregate_paper(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                        int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                        const uint8_t *I0, int pitch, int64_t *S)
+{
+    const int64_t n = (int64_t)W * H * Dw;
+    int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *F = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *B = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!Q || !F || !B) {
+        free(Q);
+        free(F);
+        free(B);
+        return -2;
+    }
+    for (int64_t i = 0; i < n; ++i) Q[i] = C[i];
+    int status = 0;
+    const int layers = num_paths / 2;
+    for (int layer = 0; layer < layers; ++layer) {
+        const int *fw = ora_dirs[2 * layer], *bw = ora_dirs[2 * layer + 1];
+        const int double_up = (fw[0] == 1 && fw[1] == 0);
+        if (ora_path_pen(Q, lo, W, H, Dw, fw[0], fw[1], p1, T, lut, I0, pitch, double_up, 1, 0,
+                         0, F))
+            status = -1;
+        if (ora_path_pen(Q, lo, W, H, Dw, bw[0], bw[1], p1, T, lut, I0, pitch, 0, 1, 0, 0, B))
+            status = -1;
+        for (int64_t i = 0; i < n; ++i)
+            Q[i] = layer == 0 ? min64(F[i], B[i]) : (F[i] + B[i]) / 2;
+    }
+    memcpy(S, Q, sizeof(int64_t) * (size_t)n);
+    free(Q);
+    free(F);
+    free(B);
+    return status;
+}
+
 /* Winner-take-all over each pixel's window, ties to the smallest disparity (R9). */
 void ora_wta(const int64_t *S, const int32_t *lo, int W, int H, int Dw, uint16_t *d)
 {
@@ -397,6 +618,10 @@ int ora_check_params(int W, int H, const ora_params *p)
     if (W0 < N || H0 < N) return -1;
     for (int l = 1; l < p->num_scales; ++l)
         if (p->block[l - 1] < 0 || p->block[l - 1] > 8) return -1;
+    if (p->merge_mode != ORA_MERGE_SUM && p->merge_mode != ORA_MERGE_PAPER) return -1;
+    if (p->grad_lut)
+        for (int g = 0; g < 256; ++g)
+            if (p->grad_lut[g] < 0 || p->grad_lut[g] > p->p1) return -1;
     const int64_t jump = (int64_t)p->p1 * (p->max_disparity - 1);
     const int64_t pen = p->trunc < jump ? p->trunc : jump;
     if ((int64_t)p->num_paths * (255 + pen) >= 65535) return -1;
@@ -469,7 +694,16 @@ static int run_view(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitc
         }
         if (l > 0) ora_seed(dprev, Wp, Hp, Wl, Hl, level_block(p, l), Dw, Dl, lo);
         ora_cost_volume(lv[l].I0, lv[l].I1, Wl, Hl, Wl, p->ssim_window, lo, Dw, C);
-        if (ora_aggregate(C, lo, Wl, Hl, Dw, p->num_paths, p->p1, T, 1, Sv)) status = -1;
+        int ag;
+        if (p->merge_mode == ORA_MERGE_PAPER)
+            ag = ora_aggregate_paper(C, lo, Wl, Hl, Dw, p->num_paths, p->p1, T, p->grad_lut,
+                                     lv[l].I0, Wl, Sv);
+        else if (p->grad_lut)
+            ag = ora_aggregate_grad(C, lo, Wl, Hl, Dw, p->num_paths, p->p1, T, p->grad_lut,
+                                    lv[l].I0, Wl, Sv);
+        else
+            ag = ora_aggregate(C, lo, Wl, Hl, Dw, p->num_paths, p->p1, T, 1, Sv);
+        if (ag) status = -1;
         ora_wta(Sv, lo, Wl, Hl, Dw, d);
         if (l == last) {
             if (lo_out) memcpy(lo_out, lo, sizeof(int32_t) * (size_t)npx);

@@ -23,6 +23,9 @@ extern "C" {
 #define ORA_INVALID 0xFFFFu
 #define ORA_NO_TRUNC 0x7FFFFFFF
 
+#define ORA_MERGE_SUM 0    /* S = sum of the directional passes (Eq. viterbi)          */
+#define ORA_MERGE_PAPER 1  /* hierarchical layers H, V, two diagonals (Section 3.2)   */
+
 typedef struct {
     int32_t max_disparity;  /* D: labels 0..D-1 at full resolution              */
     int32_t num_scales;     /* S: pyramid levels, factor 2 (Section 3.4)          */
@@ -34,6 +37,8 @@ typedef struct {
     int32_t block[4];       /* mode-block side per finer level (1 = interpolate)  */
     int32_t lr_check;       /* 1: left-right consistency check on the output      */
     int32_t lr_tol;         /* accepted |d_L - d_R| in pixels                      */
+    int32_t merge_mode;     /* ORA_MERGE_SUM or ORA_MERGE_PAPER                    */
+    const int32_t *grad_lut;/* NULL, or 256 jump slopes indexed by |I0(p) - I0(p-r)| */
 } ora_params;
 
 /* Integer SSIM constants: round(C1 * n^2), round(C2 * n^2), n = N*N. */
@@ -68,6 +73,43 @@ int ora_path(const int32_t *C, const int32_t *lo, int W, int H, int Dw, int dx, 
 /* Sum of the num_paths directional passes: S[y][x][k] (Eq. viterbi). */
 int ora_aggregate(const int32_t *C, const int32_t *lo, int W, int H, int Dw, int num_paths,
                   int64_t p1, int64_t T, int normalized, int64_t *S);
+
+/* Jump penalty of one step with separate slopes and truncations for upward jumps
+ * (u > v: the disparity grows along the scan) and downward jumps (u < v):
+ *     eps(u,v) = min(p_up (u-v), T_up)  for u > v,   min(p_dn (v-u), T_dn)  for u < v. */
+typedef struct {
+    int64_t p_up, p_dn;
+    int64_t T_up, T_dn;     /* ORA_NO_TRUNC = no truncation */
+} ora_penalty;
+
+void ora_envelope_naive_pen(const int64_t *A, int lo_prev, int lo, int Dw,
+                            const ora_penalty *e, int64_t *M);
+void ora_envelope_fast_pen(const int64_t *A, int lo_prev, int lo, int Dw,
+                           const ora_penalty *e, int64_t *M);
+
+/* Directional pass over an int64 data term Q with a penalty per step: slope
+ * P(p) = lut[|I0(p) - I0(p-r)|] when lut != NULL (Eq. EU's gradient weighting), else
+ * p1; truncation T; with double_up = 1 upward jumps cost twice (slope 2P, truncation
+ * 2T).  Output: the bounded form L = Q + M' - min_v L(p-r,v) (normalize_out = 0) or
+ * the per-pixel min-normalised Lhat(p,u) = L(p,u) - min_v L(p,v) (normalize_out = 1).
+ * Returns -1 if check = 1 and the fast and naive envelopes ever disagree.             */
+int ora_path_pen(const int64_t *Q, const int32_t *lo, int W, int H, int Dw, int dx, int dy,
+                 int64_t p1, int64_t T, const int32_t *lut, const uint8_t *I0, int pitch,
+                 int double_up, int normalize_out, int use_naive, int check, int64_t *L);
+
+/* Sum of the bounded passes with per-step (gradient) penalties; equal to
+ * ora_aggregate when lut == NULL.                                                   */
+int ora_aggregate_grad(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                       int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                       const uint8_t *I0, int pitch, int64_t *S);
+
+/* The paper's hierarchical merge: layers H, V (and the two diagonal pairs for 8
+ * paths), each a forward and a backward pass over the previous layer's output; the
+ * two normalised passes merge by min (H) or floor of the mean (other layers); the
+ * left-to-right pass charges upward jumps twice.  S = the last layer's output.      */
+int ora_aggregate_paper(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                        int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                        const uint8_t *I0, int pitch, int64_t *S);
 
 /* Winner-take-all: d = lo + argmin_k S, ties to the smallest k. */
 void ora_wta(const int64_t *S, const int32_t *lo, int W, int H, int Dw, uint16_t *d);

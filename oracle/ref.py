@@ -14,6 +14,8 @@ from . import build_oracle
 
 NO_TRUNC = 0x7FFFFFFF
 INVALID = 0xFFFF
+MERGE_SUM = 0
+MERGE_PAPER = 1
 
 _lib = None
 
@@ -30,11 +32,27 @@ class OraParams(C.Structure):
         ("block", C.c_int32 * 4),
         ("lr_check", C.c_int32),
         ("lr_tol", C.c_int32),
+        ("merge_mode", C.c_int32),
+        ("grad_lut", C.POINTER(C.c_int32)),
     ]
 
 
+class OraPenalty(C.Structure):
+    _fields_ = [("p_up", C.c_int64), ("p_dn", C.c_int64), ("T_up", C.c_int64),
+                ("T_dn", C.c_int64)]
+
+
+def _lut(grad_lut):
+    if grad_lut is None:
+        return None, None
+    a = np.ascontiguousarray(grad_lut, dtype=np.int32)
+    assert a.shape == (256,)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
 def params(max_disparity=32, num_scales=1, num_paths=4, p1=10, trunc=30, ssim_window=5,
-           window=0, block=(0, 0, 0, 0), lr_check=1, lr_tol=1):
+           window=0, block=(0, 0, 0, 0), lr_check=1, lr_tol=1, merge_mode=MERGE_SUM,
+           grad_lut=None):
     p = OraParams()
     p.max_disparity = max_disparity
     p.num_scales = num_scales
@@ -48,6 +66,10 @@ def params(max_disparity=32, num_scales=1, num_paths=4, p1=10, trunc=30, ssim_wi
         p.block[i] = blk[i]
     p.lr_check = lr_check
     p.lr_tol = lr_tol
+    p.merge_mode = merge_mode
+    p._lut_keep, ptr = _lut(grad_lut)   # the table must outlive the struct's pointer
+    if ptr is not None:
+        p.grad_lut = ptr
     return p
 
 
@@ -75,6 +97,16 @@ def lib():
         L.ora_path.restype = i
         L.ora_aggregate.argtypes = [i32p, i32p, i, i, i, i, C.c_int64, C.c_int64, i, i64p]
         L.ora_aggregate.restype = i
+        penp = C.POINTER(OraPenalty)
+        for f in (L.ora_envelope_naive_pen, L.ora_envelope_fast_pen):
+            f.argtypes = [i64p, i, i, i, penp, i64p]
+            f.restype = None
+        L.ora_path_pen.argtypes = [i64p, i32p, i, i, i, i, i, C.c_int64, C.c_int64, i32p, u8p,
+                                   i, i, i, i, i, i64p]
+        L.ora_path_pen.restype = i
+        for f in (L.ora_aggregate_grad, L.ora_aggregate_paper):
+            f.argtypes = [i32p, i32p, i, i, i, i, C.c_int64, C.c_int64, i32p, u8p, i, i64p]
+            f.restype = i
         L.ora_wta.argtypes = [i64p, i32p, i, i, i, u16p]
         L.ora_wta.restype = None
         L.ora_downsample2.argtypes = [u8p, i, i, i, u8p, i]
@@ -173,6 +205,67 @@ def aggregate(Cv, num_paths, p1, T, lo=None, normalized=True):
                              int(normalized), _p(S, C.c_int64))
     assert st == 0
     return S
+
+
+def envelope_pen(A, lo_prev, lo, p_up, p_dn, T_up, T_dn, naive=False):
+    A = np.ascontiguousarray(A, dtype=np.int64)
+    M = np.zeros(A.shape[0], np.int64)
+    e = OraPenalty(p_up, p_dn, T_up, T_dn)
+    f = lib().ora_envelope_naive_pen if naive else lib().ora_envelope_fast_pen
+    f(_p(A, C.c_int64), lo_prev, lo, A.shape[0], C.byref(e), _p(M, C.c_int64))
+    return M
+
+
+def _opt_lo(lo):
+    if lo is None:
+        return None, None
+    lo = np.ascontiguousarray(lo, dtype=np.int32)
+    return lo, _p(lo, C.c_int32)
+
+
+def _opt_img(I0, grad_lut):
+    if grad_lut is None:
+        return None, None
+    I0 = _img(I0)
+    return I0, _p(I0, C.c_uint8)
+
+
+def path_pen(Q, dx, dy, p1, T, lo=None, grad_lut=None, I0=None, double_up=False,
+             normalize_out=False, naive=False, check=False):
+    """One pass over an int64 data term with per-step penalties (ora_path_pen)."""
+    Q = np.ascontiguousarray(Q, dtype=np.int64)
+    H, W, Dw = Q.shape
+    L = np.zeros((H, W, Dw), np.int64)
+    lo, lop = _opt_lo(lo)
+    lut, lutp = _lut(grad_lut)
+    img, imgp = _opt_img(I0, grad_lut)
+    st = lib().ora_path_pen(_p(Q, C.c_int64), lop, W, H, Dw, dx, dy, p1, T, lutp, imgp, W,
+                            int(double_up), int(normalize_out), int(naive), int(check),
+                            _p(L, C.c_int64))
+    return L, st
+
+
+def _aggregate_pen(fn, Cv, num_paths, p1, T, lo, grad_lut, I0):
+    Cv = np.ascontiguousarray(Cv, dtype=np.int32)
+    H, W, Dw = Cv.shape
+    S = np.zeros((H, W, Dw), np.int64)
+    lo, lop = _opt_lo(lo)
+    lut, lutp = _lut(grad_lut)
+    img, imgp = _opt_img(I0, grad_lut)
+    st = fn(_p(Cv, C.c_int32), lop, W, H, Dw, num_paths, p1, T, lutp, imgp, W,
+            _p(S, C.c_int64))
+    assert st == 0
+    return S
+
+
+def aggregate_grad(Cv, num_paths, p1, T, lo=None, grad_lut=None, I0=None):
+    """Sum of bounded passes with gradient-weighted slopes (ora_aggregate_grad)."""
+    return _aggregate_pen(lib().ora_aggregate_grad, Cv, num_paths, p1, T, lo, grad_lut, I0)
+
+
+def aggregate_paper(Cv, num_paths, p1, T, lo=None, grad_lut=None, I0=None):
+    """The paper's layered merge (ora_aggregate_paper)."""
+    return _aggregate_pen(lib().ora_aggregate_paper, Cv, num_paths, p1, T, lo, grad_lut, I0)
 
 
 def wta(S, lo=None):
