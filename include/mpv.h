@@ -55,6 +55,12 @@ typedef enum {
 #define MPV_NO_TRUNC 0x7FFFFFFF
 
 #define MPV_MERGE_SUM 0         /* S = sum of the directional energies (Eq. viterbi)     */
+#define MPV_MERGE_PAPER 1       /* the paper's layered merge (Section 3.2, Table alg):     */
+                                /* left/right, up/down, then the two diagonal pairs; each  */
+                                /* layer's two passes run over the previous layer's merged */
+                                /* energies and merge by min (horizontal) or floor of the  */
+                                /* mean (others), after per-pixel min-normalisation; the   */
+                                /* left-to-right pass charges upward jumps twice           */
 #define MPV_PROPOSAL_PYRAMID 0  /* finer-level windows from the coarser level (Sec. 3.4) */
 #define MPV_PROPOSAL_LEARNED 1  /* finest-level windows from the learned proposal        */
 
@@ -74,7 +80,7 @@ typedef struct {
                             /* 1 = per-pixel interpolation, 0 = default (2, 1 at finest)  */
     int32_t lr_check;       /* 1: left-right check on the output, 0: raw left WTA map     */
     int32_t lr_tol;         /* accepted |d_L - d_R| in pixels (default 1)                  */
-    int32_t merge_mode;     /* MPV_MERGE_SUM                                                */
+    int32_t merge_mode;     /* MPV_MERGE_SUM or MPV_MERGE_PAPER                             */
     int32_t proposal;       /* MPV_PROPOSAL_PYRAMID or MPV_PROPOSAL_LEARNED                */
 } mpv_params;
 
@@ -132,6 +138,15 @@ mpv_status mpv_match_batch(mpv_ctx *ctx, const mpv_pair *pairs, int32_t n, void 
  * range; *lanes (may be NULL) receives the chosen lanes per scan path of the
  * aggregation (4 or 8).  Synchronous.  Results do not depend on the choice.          */
 mpv_status mpv_autotune(mpv_ctx *ctx, const mpv_pair *pair, int32_t *lanes);
+
+/* Gradient-weighted TV penalty (Eq. EU: the TV term of a step scaled by e^{-|G|}).
+ * slopes: host array of 256 integer jump slopes; the step from pixel p - r to p along a
+ * scan direction then costs min(slopes[|I0(p) - I0(p - r)|] * |du|, T) instead of
+ * min(p1 * |du|, T), I0 being the reference image of the view at the pyramid level.
+ * Each slope must lie in [0, p1] of the parameters in force when matching (checked at
+ * each match: MPV_ERR_INVALID_ARG otherwise).  The table is copied (to the device as
+ * well); NULL switches the weighting off.  Applies to both merge modes.               */
+mpv_status mpv_set_gradient_penalty(mpv_ctx *ctx, const int32_t *slopes);
 
 /* Loads the learned-proposal network (file written by paper_2001_09678_gb300/learn.py:
  * "MPVP", version 1, six layers of 3x3 convolutions, FP32 weights stored, converted to

@@ -20,9 +20,12 @@
 //    come from the neighbouring lanes by shuffles, and a window shift between
 //    consecutive pixels (pyramid levels) re-indexes the predecessor through shared
 //    memory.  S is accumulated with 64-bit reductions of four packed labels.
-//  * agg_scan: any R and window width: one warp per scan path, the two sweeps written
+//  * agg_general: any R and window width: one warp per scan path, the two sweeps written
 //    as prefix minima  min_{v<=u} A(v) + p1 (u-v) = p1 u + min_{v<=u} (A(v) - p1 v)
-//    (and the mirror image), evaluated by shuffle scans over the lanes.
+//    (and the mirror image), evaluated by shuffle scans over the lanes.  It also runs
+//    the variants: a slope per step from the image gradient (Eq. EU) and the paper's
+//    layered merge of Section 3.2 (passes stored per direction and merged by the next
+//    layer, the left-to-right pass with doubled upward jumps).
 #include "mpv_internal.cuh"
 
 namespace mpv {
@@ -320,16 +323,28 @@ void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------------
-// agg_scan (general radius and width)
+// agg_general (general radius and width, per-step penalties, layered merge)
 // ---------------------------------------------------------------------------------
 
 constexpr int kScanWarps = 8;
 
+// One warp per scan path, K labels per lane.  The envelope of the predecessor A with
+// upward slope pu (u > v) and downward slope pd (u < v) is
+//     M'(u) = min( pu u + min_{v<=u} (A(v) - pu v),   -pd u + min_{v>=u} (A(v) + pd v),
+//                  min_{v<=u} A(v) + Tu,              min_{v>=u} A(v) + T )
+// (Section 3.3's two sweeps as prefix/suffix minima over the lanes); with equal caps the
+// last two terms are min_v A(v) + T.  The slope of a step is p1, or with a gradient
+// table lut[|I0(p) - I0(p-r)|] (Eq. EU's weighting); the direction m.double_up_dir
+// charges upward jumps twice (pu = 2P, Tu = 2T: the paper's left-to-right pass).
+// Data term: the cost bytes, or the merge of the previous layer's two passes.  Output:
+// the bounded energies added into S, or the per-pixel min-normalised energies stored
+// into the direction's own volume (one layer of the paper's merge, Section 3.2).
 template <int K>
-__global__ void __launch_bounds__(kScanWarps * 32) agg_scan(LevelArgs a)
+__global__ void __launch_bounds__(kScanWarps * 32) agg_general(LevelArgs a, MergeArgs m)
 {
+    constexpr int NJ = 32 * K;                // labels covered by the warp
     const int view = blockIdx.z;
-    const int dir = blockIdx.y;
+    const int dir = m.dir0 + blockIdx.y;
     const int dx = c_dirs[dir][0], dy = c_dirs[dir][1];
     const int W = a.W, H = a.H, Dw = a.Dw, Dws = a.Dws;
     const int lane = threadIdx.x & 31;
@@ -337,80 +352,122 @@ __global__ void __launch_bounds__(kScanWarps * 32) agg_scan(LevelArgs a)
     const int path = blockIdx.x * kScanWarps + warp;
     if (path >= num_paths_dir(dx, dy, W, H)) return;
     const ViewLevel &V = a.v[view];
-    const int P1 = a.p1, T = a.trunc;
+    const int T = a.trunc;                    // finite: min(T, p1 (D_l - 1))
+    const bool dbl = dir == m.double_up_dir;
+    const int Tu = dbl ? 2 * T : T;
+    // selected without dynamic indexing, which would copy the parameter arrays to the stack
+    const uint16_t *qa = view ? m.qa[1] : m.qa[0];
+    const uint16_t *qb = view ? m.qb[1] : m.qb[0];
+    uint16_t *const *outs = view ? m.out[1] : m.out[0];
+    uint16_t *out = (dir & 1) ? outs[1] : outs[0];
 
     extern __shared__ int sh[];
-    int *pB = sh + warp * 2 * (32 * K + 2);   // [32K+1]: index j+1 holds prefix min up to j
-    int *sC = pB + (32 * K + 1);              // [32K+1]: index j holds suffix min from j
+    int *pB = sh + warp * 4 * (NJ + 2);       // [NJ+1]: index j+1 holds the prefix minimum to j
+    int *sC = pB + (NJ + 1);                  // [NJ+1]: index j holds the suffix minimum from j
+    int *pA = sC + (NJ + 1);                  // the same two for A itself (asymmetric caps)
+    int *sA = pA + (NJ + 1);
 
     int x, y;
     path_start(dx, dy, W, H, path, x, y);
     int A[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) A[t] = kInf;
-    int prev_lo = 0;
+    int prev_lo = 0, prev_i = 0;
     bool first = true;
     while (x >= 0 && x < W && y >= 0 && y < H) {
         const int64_t pix = (int64_t)y * W + x;
         const int cur_lo = V.lo ? (int)V.lo[pix] : 0;
-        const uint8_t *cp = V.C + pix * Dws;
         int c[K];
 #pragma unroll
         for (int t = 0; t < K; ++t) {
             const int k = lane * K + t;
-            c[t] = k < Dw ? (int)cp[k] : 0;
+            int v = 0;
+            if (k < Dw) {
+                if (m.in_mode == 0) {
+                    v = V.C[pix * Dws + k];
+                } else {
+                    const int ea = qa[pix * Dws + k], eb = qb[pix * Dws + k];
+                    v = m.in_mode == 1 ? min(ea, eb) : (ea + eb) >> 1;
+                }
+            }
+            c[t] = v;
         }
+        const int cur_i = m.lut ? (int)V.I0[(int64_t)y * V.pitch0 + x] : 0;
         int L[K];
         if (first) {
 #pragma unroll
             for (int t = 0; t < K; ++t) L[t] = c[t];
             first = false;
         } else {
-            int m = A[0];
+            const int P = m.lut ? min(m.lut[abs(cur_i - prev_i)], T) : a.p1;
+            const int pu = dbl ? 2 * P : P, pd = P;
+            int mn = A[0];
 #pragma unroll
-            for (int t = 1; t < K; ++t) m = min(m, A[t]);
-            const int amin = __reduce_min_sync(kFull, m);
-            int pb[K], sc[K];
-            int run = kInf;
+            for (int t = 1; t < K; ++t) mn = min(mn, A[t]);
+            const int amin = __reduce_min_sync(kFull, mn);
+            // prefix minima of A(j) - pu j (and of A), suffix minima of A(j) + pd j (and of A)
+            int pb[K], sc[K], pa[K], sa[K];
+            int run = kInf, runa = kInf;
 #pragma unroll
             for (int t = 0; t < K; ++t) {
-                run = min(run, A[t] - P1 * (lane * K + t));
+                run = min(run, A[t] - pu * (lane * K + t));
+                runa = min(runa, A[t]);
                 pb[t] = run;
+                pa[t] = runa;
             }
-            int incl = run;
+            int incl = run, incla = runa;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl = min(incl, v);
+                const int va = __shfl_up_sync(kFull, incla, o);
+                if (lane >= o) {
+                    incl = min(incl, v);
+                    incla = min(incla, va);
+                }
             }
             int excl = __shfl_up_sync(kFull, incl, 1);
-            if (lane == 0) excl = kInf;
+            int excla = __shfl_up_sync(kFull, incla, 1);
+            if (lane == 0) excl = excla = kInf;
 #pragma unroll
-            for (int t = 0; t < K; ++t) pb[t] = min(pb[t], excl);
-            run = kInf;
+            for (int t = 0; t < K; ++t) {
+                pb[t] = min(pb[t], excl);
+                pa[t] = min(pa[t], excla);
+            }
+            run = runa = kInf;
 #pragma unroll
             for (int t = K - 1; t >= 0; --t) {
-                run = min(run, A[t] + P1 * (lane * K + t));
+                run = min(run, A[t] + pd * (lane * K + t));
+                runa = min(runa, A[t]);
                 sc[t] = run;
+                sa[t] = runa;
             }
             incl = run;
+            incla = runa;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_down_sync(kFull, incl, o);
-                if (lane + o < 32) incl = min(incl, v);
+                const int va = __shfl_down_sync(kFull, incla, o);
+                if (lane + o < 32) {
+                    incl = min(incl, v);
+                    incla = min(incla, va);
+                }
             }
             excl = __shfl_down_sync(kFull, incl, 1);
-            if (lane == 31) excl = kInf;
+            excla = __shfl_down_sync(kFull, incla, 1);
+            if (lane == 31) excl = excla = kInf;
 #pragma unroll
-            for (int t = 0; t < K; ++t) sc[t] = min(sc[t], excl);
+            for (int t = 0; t < K; ++t) {
+                sc[t] = min(sc[t], excl);
+                sa[t] = min(sa[t], excla);
+            }
 
             const int s = cur_lo - prev_lo;      // uniform across the warp
-            const int cap = amin + T;
             if (s == 0) {
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
                     const int j = lane * K + t;
-                    const int M = min(min(P1 * j + pb[t], sc[t] - P1 * j), cap);
+                    int M = min(pu * j + pb[t], sc[t] - pd * j);
+                    M = dbl ? min(M, min(pa[t] + Tu, sa[t] + T)) : min(M, amin + T);
                     L[t] = c[t] + M - amin;
                 }
             } else {
@@ -418,40 +475,59 @@ __global__ void __launch_bounds__(kScanWarps * 32) agg_scan(LevelArgs a)
                 for (int t = 0; t < K; ++t) {
                     pB[lane * K + t + 1] = pb[t];
                     sC[lane * K + t] = sc[t];
+                    pA[lane * K + t + 1] = pa[t];
+                    sA[lane * K + t] = sa[t];
                 }
                 if (lane == 0) {
-                    pB[0] = kInf;
-                    sC[32 * K] = kInf;
+                    pB[0] = pA[0] = kInf;
+                    sC[NJ] = sA[NJ] = kInf;
                 }
                 __syncwarp();
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
                     const int jj = s + lane * K + t;  // label index in the predecessor window
-                    const int pi = min(max(jj, -1), 32 * K - 1) + 1;
-                    const int si = min(max(jj, 0), 32 * K);
-                    const int M = min(min(P1 * jj + pB[pi], sC[si] - P1 * jj), cap);
+                    const int pi = min(max(jj, -1), NJ - 1) + 1;
+                    const int si = min(max(jj, 0), NJ);
+                    int M = min(pu * jj + pB[pi], sC[si] - pd * jj);
+                    M = dbl ? min(M, min(pA[pi] + Tu, sA[si] + T)) : min(M, amin + T);
                     L[t] = c[t] + M - amin;
                 }
                 __syncwarp();
             }
         }
-        // S: packed 16-bit pairs, padding labels add nothing
+        // padding labels: never a predecessor, add nothing, stored as 0
 #pragma unroll
         for (int t = 0; t < K; ++t) {
             const int k = lane * K + t;
             if (k >= Dw) L[t] = 0;
         }
-        uint16_t *sp = V.S + pix * Dws;
-        if (K == 1) {
-            const int up = __shfl_down_sync(kFull, L[0], 1);
-            if ((lane & 1) == 0 && lane < Dws)
-                atomicAdd((unsigned int *)(sp + lane), (unsigned)L[0] | ((unsigned)up << 16));
-        } else {
+        if (m.out_mode == 0) {
+            // S: packed 16-bit pairs
+            uint16_t *sp = V.S + pix * Dws;
+            if (K == 1) {
+                const int up = __shfl_down_sync(kFull, L[0], 1);
+                if ((lane & 1) == 0 && lane < Dws)
+                    atomicAdd((unsigned int *)(sp + lane), (unsigned)L[0] | ((unsigned)up << 16));
+            } else {
 #pragma unroll
-            for (int t = 0; t < K; t += 2) {
+                for (int t = 0; t < K; t += 2) {
+                    const int k = lane * K + t;
+                    if (k < Dws)
+                        atomicAdd((unsigned int *)(sp + k),
+                                  (unsigned)L[t] | ((unsigned)L[t + 1] << 16));
+                }
+            }
+        } else {
+            int lm = kInf;
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+                if (lane * K + t < Dw) lm = min(lm, L[t]);
+            const int lmin = __reduce_min_sync(kFull, lm);
+            uint16_t *op = out + pix * Dws;
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
                 const int k = lane * K + t;
-                if (k < Dws)
-                    atomicAdd((unsigned int *)(sp + k), (unsigned)L[t] | ((unsigned)L[t + 1] << 16));
+                if (k < Dws) op[k] = (uint16_t)(k < Dw ? L[t] - lmin : 0);
             }
         }
 #pragma unroll
@@ -460,22 +536,34 @@ __global__ void __launch_bounds__(kScanWarps * 32) agg_scan(LevelArgs a)
             A[t] = k < Dw ? L[t] : kInf;
         }
         prev_lo = cur_lo;
+        prev_i = cur_i;
         x += dx;
         y += dy;
     }
 }
 
 template <int K>
-void launch_scan(const LevelArgs &a, cudaStream_t s)
+void launch_general_k(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
 {
     const int maxp = a.W + a.H - 1;
-    dim3 grid((maxp + kScanWarps - 1) / kScanWarps, a.npaths, a.nviews);
-    const size_t smem = sizeof(int) * kScanWarps * 2 * (32 * K + 2);
-    cudaFuncSetAttribute(agg_scan<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    agg_scan<K><<<grid, kScanWarps * 32, smem, s>>>(a);
+    dim3 grid((maxp + kScanWarps - 1) / kScanWarps, m.ndirs, a.nviews);
+    const size_t smem = sizeof(int) * kScanWarps * 4 * (32 * K + 2);
+    cudaFuncSetAttribute(agg_general<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    agg_general<K><<<grid, kScanWarps * 32, smem, s>>>(a, m);
 }
 
 }  // namespace
+
+void launch_aggregate_general(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
+{
+    const int K = (a.Dw + 31) / 32;
+    if (K <= 1) launch_general_k<1>(a, m, s);
+    else if (K <= 2) launch_general_k<2>(a, m, s);
+    else if (K <= 4) launch_general_k<4>(a, m, s);
+    else if (K <= 8) launch_general_k<8>(a, m, s);
+    else if (K <= 16) launch_general_k<16>(a, m, s);
+    else launch_general_k<32>(a, m, s);
+}
 
 void launch_aggregate(const LevelArgs &a, cudaStream_t s)
 {
@@ -494,13 +582,14 @@ void launch_aggregate(const LevelArgs &a, cudaStream_t s)
             return;
         }
     }
-    const int K = (a.Dw + 31) / 32;
-    if (K <= 1) launch_scan<1>(a, s);
-    else if (K <= 2) launch_scan<2>(a, s);
-    else if (K <= 4) launch_scan<4>(a, s);
-    else if (K <= 8) launch_scan<8>(a, s);
-    else if (K <= 16) launch_scan<16>(a, s);
-    else launch_scan<32>(a, s);
+    MergeArgs m{};
+    m.in_mode = 0;
+    m.out_mode = 0;
+    m.dir0 = 0;
+    m.ndirs = a.npaths;
+    m.double_up_dir = -1;
+    m.lut = nullptr;
+    launch_aggregate_general(a, m, s);
 }
 
 }  // namespace mpv

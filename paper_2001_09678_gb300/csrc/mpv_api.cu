@@ -48,6 +48,12 @@ struct mpv_ctx {
     ProposalNet net;
     void *net_mem = nullptr;
     unsigned long long *edge_host = nullptr;   // pinned: window-edge hits, pixels
+    // gradient-weighted penalty: host copy and device copy of the 256 slopes
+    bool grad_on = false;
+    int32_t grad_host[256] = {};
+    int *grad_dev = nullptr;
+
+    const int *lut() const { return grad_on ? grad_dev : nullptr; }
 };
 
 namespace {
@@ -152,6 +158,15 @@ mpv_status ensure_batch_streams(mpv_ctx *ctx)
     return MPV_OK;
 }
 
+// The gradient table's slopes must not exceed p1 (the energy bounds are derived from p1).
+mpv_status check_grad(const mpv_ctx *ctx)
+{
+    if (!ctx->grad_on) return MPV_OK;
+    for (int g = 0; g < 256; ++g)
+        if (ctx->grad_host[g] < 0 || ctx->grad_host[g] > ctx->p.p1) return MPV_ERR_INVALID_ARG;
+    return MPV_OK;
+}
+
 void drop_graphs(mpv_ctx *ctx)
 {
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
@@ -163,6 +178,7 @@ void drop_graphs(mpv_ctx *ctx)
 // the same bit-exact result; only the time differs.
 mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
 {
+    if (check_grad(ctx) != MPV_OK) return MPV_ERR_INVALID_ARG;
     const uint64_t key = shape_key(ctx->p, job.W, job.H, job.D);
     auto it = ctx->tuning.find(key);
     if (it != ctx->tuning.end()) {
@@ -175,8 +191,7 @@ mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
     cudaStreamSynchronize(ctx->last_stream);
     Geometry g;
     make_geometry(ctx->p, job.W, job.H, job.D, g);
-    st = ensure_workspace(ctx, make_layout(g, views_needed(ctx->p, job, nullptr),
-                                           ctx->p.proposal == MPV_PROPOSAL_LEARNED).total);
+    st = ensure_workspace(ctx, make_layout(g, views_needed(ctx->p, job, nullptr), ctx->p).total);
     if (st != MPV_OK) return st;
     cudaStream_t s = ctx->workers[0];
     cudaEvent_t e0, e1;
@@ -188,11 +203,13 @@ mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
     for (int c : cands) {
         Tuning t;
         t.lanes = c;
-        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t, &ctx->net);
+        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t, &ctx->net,
+                     ctx->lut());
         float tot = 0.f;
         for (int r = 0; r < 2; ++r) {
             cudaEventRecord(e0, s);
-            enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t, &ctx->net);
+            enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t, &ctx->net,
+                         ctx->lut());
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -219,6 +236,7 @@ mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
 // is cached by the batch signature and replayed by a single graph launch.
 mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stream)
 {
+    if (check_grad(ctx) != MPV_OK) return MPV_ERR_INVALID_ARG;
     mpv_status st = ensure_batch_streams(ctx);
     if (st != MPV_OK) return st;
     std::vector<Tuning> tune(n);
@@ -239,8 +257,7 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
         worker[i] = r % nw;
         Geometry g;
         make_geometry(ctx->p, jobs[i].W, jobs[i].H, jobs[i].D, g);
-        const size_t b = make_layout(g, views_needed(ctx->p, jobs[i], nullptr),
-                                     ctx->p.proposal == MPV_PROPOSAL_LEARNED).total;
+        const size_t b = make_layout(g, views_needed(ctx->p, jobs[i], nullptr), ctx->p).total;
         wbytes[worker[i]] = std::max(wbytes[worker[i]], b);
     }
     size_t total = 0;
@@ -265,6 +282,7 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
         ctx->bws_bytes = total;
     }
     uint64_t sig = mix64(shape_key(ctx->p, n, nw, 0), (uint64_t)(uintptr_t)ctx->bws);
+    sig = mix64(sig, (uint64_t)(uintptr_t)ctx->lut());
     for (int i = 0; i < n; ++i) {
         const PairJob &j = jobs[i];
         sig = mix64(sig, (uint64_t)(uintptr_t)j.left);
@@ -294,7 +312,7 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
         const int i = order[r];
         const int w = worker[i];
         est = enqueue_pair(ctx->p, jobs[i], (uint8_t *)ctx->bws + woff[w], ctx->workers[w],
-                           nullptr, nullptr, tune[i], &ctx->net);
+                           nullptr, nullptr, tune[i], &ctx->net, ctx->lut());
     }
     for (int w = 0; w < nw; ++w) {
         cudaEventRecord(ctx->joins[w], ctx->workers[w]);
@@ -324,10 +342,10 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
 // Enqueues one pair with the context's workspace and profiler.
 mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const StageSink *dbg)
 {
+    if (check_grad(ctx) != MPV_OK) return MPV_ERR_INVALID_ARG;
     Geometry g;
     make_geometry(ctx->p, job.W, job.H, job.D, g);
-    const Layout L = make_layout(g, views_needed(ctx->p, job, dbg),
-                                 ctx->p.proposal == MPV_PROPOSAL_LEARNED);
+    const Layout L = make_layout(g, views_needed(ctx->p, job, dbg), ctx->p);
     const mpv_status st = ensure_workspace(ctx, L.total);
     if (st != MPV_OK) return st;
     StageHook hook{hook_begin, hook_end, ctx};
@@ -336,7 +354,8 @@ mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const Stage
     if (it != ctx->tuning.end()) t = it->second;
     const bool learned = ctx->p.proposal == MPV_PROPOSAL_LEARNED;
     if (learned && !ctx->net.layers) return MPV_ERR_INVALID_ARG;    // no weights loaded
-    mpv_status r = enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t, &ctx->net);
+    mpv_status r =
+        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t, &ctx->net, ctx->lut());
     if (r == MPV_OK && learned && !dbg) {
         if (!ctx->edge_host) {
             if (cudaMallocHost(&ctx->edge_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
@@ -345,7 +364,7 @@ mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const Stage
             }
             ctx->edge_host[0] = ctx->edge_host[1] = 0;
         }
-        const Layout L = make_layout(g, views_needed(ctx->p, job, dbg), true);
+        const Layout L = make_layout(g, views_needed(ctx->p, job, dbg), ctx->p);
         cudaMemcpyAsync(ctx->edge_host, (uint8_t *)ctx->ws + L.edge,
                         2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
         r = cuda_status(cudaGetLastError());
@@ -615,11 +634,39 @@ mpv_status mpv_proposal_features(mpv_ctx *ctx, const uint8_t *left, const uint8_
     DeviceGuard guard(ctx->device);
     Geometry g;
     make_geometry(p, width, height, p.max_disparity, g);
-    const mpv_status st = ensure_workspace(ctx, make_layout(g, view == 1 ? 2 : 1).total);
+    const mpv_status st = ensure_workspace(ctx, make_layout(g, view == 1 ? 2 : 1, p).total);
     if (st != MPV_OK) return st;
     const PairJob job{left, right, width, height, pitch, p.max_disparity, nullptr, width, nullptr};
     return enqueue_features(p, job, (uint8_t *)ctx->ws, (cudaStream_t)cuda_stream, view,
                             (__nv_bfloat16 *)out);
+}
+
+mpv_status mpv_set_gradient_penalty(mpv_ctx *ctx, const int32_t *slopes)
+{
+    if (!ctx) return MPV_ERR_INVALID_ARG;
+    if (!slopes) {
+        ctx->grad_on = false;   // cached batch graphs are keyed by the table pointer
+        return MPV_OK;
+    }
+    for (int g = 0; g < 256; ++g)
+        if (slopes[g] < 0) return MPV_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    if (!ctx->grad_dev) {
+        const cudaError_t e = cudaMalloc(&ctx->grad_dev, 256 * sizeof(int));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->grad_dev = nullptr;
+            return cuda_status(e);
+        }
+    }
+    // earlier matches may still read the table on the caller's stream
+    cudaStreamSynchronize(ctx->last_stream);
+    const cudaError_t e =
+        cudaMemcpy(ctx->grad_dev, slopes, 256 * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int g = 0; g < 256; ++g) ctx->grad_host[g] = slopes[g];
+    ctx->grad_on = true;
+    return MPV_OK;
 }
 
 mpv_status mpv_proposal_stats(const mpv_ctx *ctx, uint64_t *edge_hits, uint64_t *pixels)
@@ -648,7 +695,7 @@ mpv_status mpv_workspace_bytes(const mpv_ctx *ctx, int32_t width, int32_t height
     if (!ctx || !bytes || width < 1 || height < 1) return MPV_ERR_INVALID_ARG;
     Geometry g;
     make_geometry(ctx->p, width, height, ctx->p.max_disparity, g);
-    *bytes = make_layout(g, ctx->p.lr_check ? 2 : 1).total;
+    *bytes = make_layout(g, ctx->p.lr_check ? 2 : 1, ctx->p).total;
     return MPV_OK;
 }
 
@@ -773,6 +820,7 @@ void mpv_destroy(mpv_ctx *ctx)
             cudaFree(ctx->bws);
         }
         if (ctx->net_mem) cudaFree(ctx->net_mem);
+        if (ctx->grad_dev) cudaFree(ctx->grad_dev);
         if (ctx->edge_host) cudaFreeHost(ctx->edge_host);
     }
     if (ctx->ws || ctx->stage) {

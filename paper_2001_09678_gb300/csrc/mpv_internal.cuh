@@ -29,6 +29,8 @@ struct ViewLevel {
     uint8_t *C;              // cost volume [H][W][Dws], u fastest (costs are <= 255)
     uint16_t *S;             // summed path energies [H][W][Dws]
     uint16_t *d;             // pre-check WTA map [H][W]
+    const uint16_t *S2;      // layered merge: the final layer's second pass (WTA and the
+                             // stage dump read floor((S + S2) / 2)); nullptr otherwise
 };
 
 struct LevelArgs {
@@ -75,6 +77,19 @@ void launch_down2(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s)
 void launch_seed(const SeedArgs &a, cudaStream_t s);
 void launch_cost(const LevelArgs &a, cudaStream_t s);
 void launch_aggregate(const LevelArgs &a, cudaStream_t s);
+
+// General passes (any radius and width, per-step penalties, layered merge).
+struct MergeArgs {
+    int in_mode;            // data term: 0 cost bytes C, 1 min(qa, qb), 2 floor((qa + qb) / 2)
+    int out_mode;           // 0 add the bounded energies into S, 1 store the per-pixel
+                            //   min-normalised energies into out[view][direction parity]
+    int dir0, ndirs;        // scan directions dir0 .. dir0 + ndirs - 1
+    int double_up_dir;      // direction whose upward jumps cost twice, -1 for none
+    const int *lut;         // 256 slopes indexed by |I0(p) - I0(p-r)|, or nullptr (p1)
+    const uint16_t *qa[kMaxViews], *qb[kMaxViews];
+    uint16_t *out[kMaxViews][2];
+};
+void launch_aggregate_general(const LevelArgs &a, const MergeArgs &m, cudaStream_t s);
 void launch_wta(const LevelArgs &a, cudaStream_t s);
 void launch_lr(const uint16_t *dL, const uint16_t *dRm, int W, int H, int tol, int check,
                uint16_t *out, int out_pitch, uint16_t *out_right, int right_pitch,
@@ -116,6 +131,7 @@ struct Layout {
     size_t img0[kMaxViews][kMaxScales], img1[kMaxViews][kMaxScales];
     size_t lo[kMaxViews][kMaxScales], d[kMaxViews][kMaxScales];
     size_t C[kMaxViews], S[kMaxViews];
+    size_t X[kMaxViews][3] = {};                  // layered merge: three more volumes per view
     size_t feat = 0, act0 = 0, act1 = 0, q = 0;   // learned proposal (both views)
     size_t edge = 0;                              // edge-hit counters
 };
@@ -145,7 +161,7 @@ struct StageSink {
 bool params_valid(const mpv_params &p);
 mpv_status validate_pair(const mpv_params &p, int W, int H, int pitch, int disp_pitch, int D);
 void make_geometry(const mpv_params &p, int W, int H, int D, Geometry &g);
-Layout make_layout(const Geometry &g, int nviews, bool learned = false);
+Layout make_layout(const Geometry &g, int nviews, const mpv_params &p);
 // Window width of the finest level under the learned proposal (centre +- 8 by default).
 int learned_window(const mpv_params &p, int D);
 int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg);
@@ -154,7 +170,8 @@ int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg);
 // (at least make_layout(...).total bytes).
 mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *workspace,
                         cudaStream_t s, const StageHook *hook, const StageSink *dbg,
-                        const Tuning &tune = Tuning(), const ProposalNet *net = nullptr);
+                        const Tuning &tune = Tuning(), const ProposalNet *net = nullptr,
+                        const int *grad_lut = nullptr);
 // Network input of the top level of `view` (2 + D_top channels, BF16) into out.
 mpv_status enqueue_features(const mpv_params &p, const PairJob &job, uint8_t *workspace,
                             cudaStream_t s, int view, __nv_bfloat16 *out);

@@ -61,7 +61,7 @@ extern "C" mpv_status mpv_match_noalloc(const mpv_params *params, const uint8_t 
                       nullptr};
     Geometry g;
     make_geometry(p, width, height, p.max_disparity, g);
-    const Layout L = make_layout(g, views_needed(p, job, nullptr));
+    const Layout L = make_layout(g, views_needed(p, job, nullptr), p);
     if (L.total > (size_t)MPV_NOALLOC_SCRATCH_BYTES) return MPV_ERR_INVALID_ARG;
 
     int device = -1;

@@ -50,7 +50,7 @@ bool params_valid(const mpv_params &p)
     if (p.max_disparity < 1 || p.max_disparity > 1024) return false;
     if (p.p1 < 0 || p.trunc < 0 || p.window < 0 || p.lr_tol < 0) return false;
     if (p.lr_check != 0 && p.lr_check != 1) return false;
-    if (p.merge_mode != MPV_MERGE_SUM) return false;
+    if (p.merge_mode != MPV_MERGE_SUM && p.merge_mode != MPV_MERGE_PAPER) return false;
     if (p.proposal != MPV_PROPOSAL_PYRAMID && p.proposal != MPV_PROPOSAL_LEARNED) return false;
     for (int i = 0; i < 4; ++i)
         if (p.block[i] < 0 || p.block[i] > 8) return false;
@@ -108,8 +108,10 @@ int learned_window(const mpv_params &p, int D)
     return w < D ? w : D;
 }
 
-Layout make_layout(const Geometry &g, int nviews, bool learned)
+Layout make_layout(const Geometry &g, int nviews, const mpv_params &p)
 {
+    const bool learned = p.proposal == MPV_PROPOSAL_LEARNED;
+    const bool layered = p.merge_mode == MPV_MERGE_PAPER;
     Layout L;
     size_t off = 0;
     int64_t maxvol = 0;
@@ -128,6 +130,8 @@ Layout make_layout(const Geometry &g, int nviews, bool learned)
         }
         L.C[v] = take(off, sizeof(uint8_t) * (size_t)maxvol);
         L.S[v] = take(off, sizeof(uint16_t) * (size_t)maxvol);
+        if (layered)
+            for (int i = 0; i < 3; ++i) L.X[v][i] = take(off, sizeof(uint16_t) * (size_t)maxvol);
     }
     if (learned) {
         const size_t px0 = (size_t)g.W[0] * g.H[0];
@@ -150,7 +154,7 @@ mpv_status enqueue_features(const mpv_params &p, const PairJob &job, uint8_t *ba
     Geometry g;
     make_geometry(q, job.W, job.H, job.D, g);
     const int nviews = view == 1 ? 2 : 1;
-    const Layout L = make_layout(g, nviews);
+    const Layout L = make_layout(g, nviews, q);
     // run the top level's cost (a debug stage of level 0), then build the features
     StageSink dbg;
     dbg.view = view;
@@ -174,7 +178,7 @@ int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg)
 
 mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, cudaStream_t s,
                         const StageHook *hook, const StageSink *dbg, const Tuning &tune,
-                        const ProposalNet *net)
+                        const ProposalNet *net, const int *grad_lut)
 {
     Geometry g;
     make_geometry(p, job.W, job.H, job.D, g);
@@ -185,7 +189,8 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             return MPV_ERR_INVALID_ARG;
         if (dbg && dbg->level != 0 && dbg->level != g.S - 1) return MPV_ERR_INVALID_ARG;
     }
-    const Layout L = make_layout(g, nviews, learned);
+    const Layout L = make_layout(g, nviews, p);
+    const bool layered = p.merge_mode == MPV_MERGE_PAPER;
     unsigned long long *edge = (unsigned long long *)(base + L.edge);
     const int S = g.S;
     const int top = S - 1;
@@ -254,6 +259,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             vl.C = base + L.C[v];
             vl.S = (uint16_t *)(base + L.S[v]);
             vl.d = (uint16_t *)(base + L.d[v][l]);
+            vl.S2 = nullptr;
         }
         a.edge = (learned && l == top) ? edge : nullptr;
         if (learned && l == top) {
@@ -306,12 +312,55 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             }
             if (!(dbg && dbg->level == 0)) continue;
         }
-        {
+        if (layered) {
+            // Section 3.2: layers of two opposite passes over the previous layer's merged
+            // energies; volumes B0..B3 per view, layer k writes (B0,B1) for even k and
+            // (B2,B3) for odd k, so the last layer's pair is always (B2,B3)
+            const int layers = p.num_paths / 2;
+            HookScope hs(hook, MPV_STAGE_AGGREGATE, layers, s);
+            uint16_t *B[kMaxViews][4];
+            for (int v = 0; v < nviews; ++v) {
+                B[v][0] = a.v[v].S;
+                for (int i = 0; i < 3; ++i) B[v][i + 1] = (uint16_t *)(base + L.X[v][i]);
+            }
+            for (int k = 0; k < layers; ++k) {
+                MergeArgs m{};
+                m.in_mode = k == 0 ? 0 : (k == 1 ? 1 : 2);   // min after the horizontal layer
+                m.out_mode = 1;
+                m.dir0 = 2 * k;
+                m.ndirs = 2;
+                m.double_up_dir = 0;                       // left to right
+                m.lut = grad_lut;
+                const int in = (k & 1) ? 0 : 2, out = (k & 1) ? 2 : 0;
+                for (int v = 0; v < nviews; ++v) {
+                    m.qa[v] = B[v][in];
+                    m.qb[v] = B[v][in + 1];
+                    m.out[v][0] = B[v][out];
+                    m.out[v][1] = B[v][out + 1];
+                }
+                launch_aggregate_general(a, m, s);
+            }
+            for (int v = 0; v < nviews; ++v) {
+                a.v[v].S = B[v][2];
+                a.v[v].S2 = B[v][3];
+            }
+        } else {
             HookScope hs(hook, MPV_STAGE_AGGREGATE, 1, s);
             const size_t vol = (size_t)a.W * a.H * a.Dws;
             for (int v = 0; v < nviews; ++v)
                 cudaMemsetAsync(a.v[v].S, 0, vol * sizeof(uint16_t), s);
-            launch_aggregate(a, s);
+            if (grad_lut) {
+                MergeArgs m{};
+                m.in_mode = 0;
+                m.out_mode = 0;
+                m.dir0 = 0;
+                m.ndirs = a.npaths;
+                m.double_up_dir = -1;
+                m.lut = grad_lut;
+                launch_aggregate_general(a, m, s);
+            } else {
+                launch_aggregate(a, s);
+            }
         }
         {
             HookScope hs(hook, MPV_STAGE_WTA, 1, s);

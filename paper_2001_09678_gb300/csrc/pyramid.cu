@@ -99,9 +99,17 @@ __global__ void wta_kernel(LevelArgs a)
     uint32_t best = 0xFFFFFFFFu;
     if (in) {
         const uint16_t *s = v.S + i * a.Dws;
-        for (int k = sub; k < a.Dw; k += 4) {
-            const uint32_t key = ((uint32_t)s[k] << 16) | (uint32_t)k;
-            best = min(best, key);
+        if (v.S2) {   // layered merge: the last layer's two passes, floor of the mean
+            const uint16_t *s2 = v.S2 + i * a.Dws;
+            for (int k = sub; k < a.Dw; k += 4) {
+                const uint32_t e = ((uint32_t)s[k] + (uint32_t)s2[k]) >> 1;
+                best = min(best, (e << 16) | (uint32_t)k);
+            }
+        } else {
+            for (int k = sub; k < a.Dw; k += 4) {
+                const uint32_t key = ((uint32_t)s[k] << 16) | (uint32_t)k;
+                best = min(best, key);
+            }
         }
     }
     best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 1));
@@ -132,7 +140,10 @@ __global__ void unpack_kernel(LevelArgs a, int view, uint16_t *cost, uint32_t *s
     const int k = (int)(e - pix * a.Dw);
     const ViewLevel &v = a.v[view];
     if (cost) cost[e] = v.C[pix * a.Dws + k];
-    if (sum) sum[e] = v.S[pix * a.Dws + k];
+    if (sum) {
+        const int64_t j = pix * a.Dws + k;
+        sum[e] = v.S2 ? ((uint32_t)v.S[j] + (uint32_t)v.S2[j]) >> 1 : v.S[j];
+    }
 }
 
 // Left-right check.  dRm is the right view's map in mirrored coordinates.

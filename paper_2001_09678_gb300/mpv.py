@@ -10,6 +10,8 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmpv.so")
 
@@ -23,6 +25,7 @@ MPV_ERR_INTERNAL = 6
 MPV_INVALID = 0xFFFF
 MPV_NO_TRUNC = 0x7FFFFFFF
 MPV_MERGE_SUM = 0
+MPV_MERGE_PAPER = 1
 MPV_PROPOSAL_PYRAMID = 0
 MPV_PROPOSAL_LEARNED = 1
 
@@ -79,6 +82,7 @@ class mpv_pair(C.Structure):
 EXPORTS = [
     "mpv_default_params", "mpv_create", "mpv_set_params", "mpv_get_params", "mpv_match",
     "mpv_match_host", "mpv_match_batch", "mpv_load_proposal_weights", "mpv_sync",
+    "mpv_set_gradient_penalty",
     "mpv_workspace_bytes", "mpv_set_workspace_limit", "mpv_debug_stage", "mpv_level_info",
     "mpv_status_string", "mpv_destroy", "mpv_profile_enable", "mpv_profile_read",
     "mpv_match_noalloc", "mpv_autotune", "mpv_server_create", "mpv_server_add_camera",
@@ -111,6 +115,7 @@ def load(path: str = LIB_PATH):
     L.mpv_match_host.argtypes = [ctx, vp, vp, i32, i32, i32, vp, i32, vp]
     L.mpv_match_batch.argtypes = [ctx, C.POINTER(mpv_pair), i32, vp]
     L.mpv_load_proposal_weights.argtypes = [ctx, C.c_char_p]
+    L.mpv_set_gradient_penalty.argtypes = [ctx, C.POINTER(C.c_int32)]
     L.mpv_sync.argtypes = [ctx]
     L.mpv_workspace_bytes.argtypes = [ctx, i32, i32, C.POINTER(C.c_size_t)]
     L.mpv_set_workspace_limit.argtypes = [ctx, C.c_size_t]
@@ -256,6 +261,18 @@ def mpv_autotune(ctx, pair) -> int:
     lanes = C.c_int32()
     _check(load().mpv_autotune(ctx, arr, C.byref(lanes)), "mpv_autotune")
     return lanes.value
+
+
+def mpv_set_gradient_penalty(ctx, slopes) -> None:
+    """256 integer jump slopes indexed by |I0(p) - I0(p-r)| (None: plain p1)."""
+    if slopes is None:
+        _check(load().mpv_set_gradient_penalty(ctx, None), "mpv_set_gradient_penalty")
+        return
+    a = np.ascontiguousarray(slopes, dtype=np.int32)
+    if a.shape != (256,):
+        raise ValueError("the gradient table has 256 entries")
+    _check(load().mpv_set_gradient_penalty(ctx, a.ctypes.data_as(C.POINTER(C.c_int32))),
+           "mpv_set_gradient_penalty")
 
 
 def mpv_load_proposal_weights(ctx, path: str) -> None:
