@@ -8,6 +8,10 @@ standing in for the paper's driving sequences.  Metric: Mdisp-evals/s = W*H*D / 
 time (nominal full-range labels of one view), plus fps and p50/p99 latency.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                  [--variant plain|paper|gradient|paper_gradient] [--workload frame|batch64]
+
+--variant selects the paper's layered path merge (Section 3.2) and/or the
+gradient-weighted TV penalty (Eq. EU, slopes round(p1 e^{-g/16})) on the same pair.
 
 --impl reference times the CPU oracle (single-threaded C) on a bounded sample of the
 same workload: the reference arm of this method is the oracle.  Under torchrun every
@@ -36,6 +40,29 @@ CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 L2_FLUSH_BYTES = 256 << 20
+GRAD_SIGMA = 16.0
+VARIANTS = {          # merge mode, gradient weighting
+    "plain": (0, False),
+    "paper": (1, False),
+    "gradient": (0, True),
+    "paper_gradient": (1, True),
+}
+
+
+def gradient_table(p1=PARAMS["p1"], sigma=GRAD_SIGMA):
+    """256 integer slopes round(p1 e^{-g / sigma}): Eq. EU's e^{-|G|} weighting with a scale."""
+    import numpy as np
+    g = np.arange(256, dtype=np.float64)
+    return np.floor(p1 * np.exp(-g / sigma) + 0.5).astype(np.int32)
+
+
+def variant_names(variant):
+    """Metric and workload strings of a variant (the plain matcher keeps the headline's)."""
+    if variant == "plain":
+        return METRIC, WORKLOAD
+    merge, grad = VARIANTS[variant]
+    tag = " + ".join(t for t, on in (("layered merge", merge), ("gradient TV", grad)) if on)
+    return METRIC[:-1] + ", " + tag + ")", WORKLOAD + ", " + tag
 
 
 def dist_env():
@@ -68,19 +95,28 @@ def level_geometry():
     return levels
 
 
-def algorithmic_bytes(views=2):
+def algorithmic_bytes(views=2, variant="plain"):
     """Minimum HBM bytes per frame of each stage: the cost kernel reads both images and
     writes the cost volume (1 B/node: costs are <= 255); the aggregation reads it
     (1 B/node) and writes the uint16 summed volume (2 B/node); winner-take-all reads
-    that (2 B/node) and writes the uint16 map."""
+    that (2 B/node) and writes the uint16 map.  The layered merge stores each pass
+    (2 B/node per direction) and reads the previous layer's pair (4 B/node per
+    direction; the first layer reads the cost bytes), and its WTA reads the last pair."""
+    merge, grad = VARIANTS[variant]
+    layers = PARAMS["num_paths"] // 2
     cost = agg = wta = 0
     nodes = 0
     for (w, h, Dl, Dw) in level_geometry():
         n = w * h * Dw
         nodes += n
         cost += views * (n + 2 * w * h)
-        agg += views * (n + 2 * n + 2 * w * h)
-        wta += views * (2 * n + 2 * w * h + 2 * w * h)
+        img = 2 * w * h if grad else 0          # the reference image, read by the passes
+        if merge:
+            agg += views * ((2 * n + 4 * n) + (layers - 1) * (8 * n + 4 * n) + img)
+            wta += views * (4 * n + 2 * w * h + 2 * w * h)
+        else:
+            agg += views * (n + 2 * n + 2 * w * h + img)
+            wta += views * (2 * n + 2 * w * h + 2 * w * h)
     return dict(cost=cost, aggregate=agg, wta=wta), nodes
 
 
@@ -196,7 +232,11 @@ def run_mine(args):
     disp = torch.empty((H, W), dtype=torch.int16, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = mpv.mpv_create(local)
-    mpv.mpv_set_params(ctx, mpv.mpv_default_params(**PARAMS))
+    merge, grad = VARIANTS[args.variant]
+    mpv.mpv_set_params(ctx, mpv.mpv_default_params(merge_mode=merge, **PARAMS))
+    if grad:
+        mpv.mpv_set_gradient_penalty(ctx, gradient_table())
+    metric, workload = variant_names(args.variant)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     for _ in range(args.warmup):
@@ -252,7 +292,7 @@ def run_mine(args):
     ok = np.array_equal(hd.numpy(), disp.cpu().numpy())
 
     # roofline of the dominant kernel (by device time over the timed region)
-    alg, nodes = algorithmic_bytes()
+    alg, nodes = algorithmic_bytes(variant=args.variant)
     stage_ms = {k: v[0] for k, v in prof.items()}
     launches = sum(v[1] for v in prof.values())
     dom = max(("cost", "aggregate", "wta"), key=lambda k: stage_ms[k])
@@ -265,11 +305,11 @@ def run_mine(args):
     if rank == 0:
         clk = clocks.summary()
         out = {
-            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "metric": metric, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "width": W, "height": H, "max_disparity": D,
+            "config": {"workload": workload, "width": W, "height": H, "max_disparity": D,
                        "scales": 3, "paths": 8, "global_batch": world,
                        "parallelism": f"replicas{world}",
                        "l2": "flushed between timed steps (256 MiB device write, untimed)"},
@@ -299,7 +339,7 @@ def run_mine(args):
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_full(L, R)
+        out["cpu_baseline"] = cpu_baseline_full(L, R, args.variant)
     if out is not None:
         print(json.dumps(out), flush=True)
 
@@ -308,15 +348,17 @@ def run_mine(args):
 # The oracle on the host
 # ------------------------------------------------------------------------------------
 
-def _ora_params():
+def _ora_params(variant="plain"):
     from oracle import ref
-    return ref.params(window=0, block=(0, 0, 0, 0), **PARAMS)
+    merge, grad = VARIANTS[variant]
+    return ref.params(window=0, block=(0, 0, 0, 0), merge_mode=merge,
+                      grad_lut=gradient_table() if grad else None, **PARAMS)
 
 
-def cpu_baseline_full(L, R):
+def cpu_baseline_full(L, R, variant="plain"):
     """The oracle, single-threaded, on one full pair of the workload (both views)."""
     from oracle import ref
-    p = _ora_params()
+    p = _ora_params(variant)
     ref.lib()
     t = time.perf_counter()
     ref.match(L, R, p)
@@ -339,7 +381,8 @@ def run_reference(args):
     rows = int(min(180, max(20, 8000 // max(1, args.steps + args.warmup))))
     y0 = (H - rows) // 2
     Ls, Rs = L[y0:y0 + rows].copy(), R[y0:y0 + rows].copy()
-    p = _ora_params()
+    p = _ora_params(args.variant)
+    metric, workload = variant_names(args.variant)
     ref.lib()
     for _ in range(args.warmup):
         ref.match(Ls, Rs, p)
@@ -353,11 +396,11 @@ def run_reference(args):
     value = args.steps * units / tot / 1e6
     sample = f"1280x{rows} strip (rows {y0}..{y0 + rows - 1}) of the 1280x720 pair per step"
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+        "impl": "reference", "metric": metric, "value": round(value, 3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * tot / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "width": W, "height": H, "max_disparity": D,
+        "config": {"workload": workload, "width": W, "height": H, "max_disparity": D,
                    "scales": 3, "paths": 8},
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -422,12 +465,14 @@ def _gen_pair(spec):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("mine", "reference"), default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=("frame", "batch64"), default="frame",
                     help="frame: the 1280x720 D=128 pair (default); batch64: the mixed batch")
+    ap.add_argument("--variant", choices=tuple(VARIANTS), default="plain",
+                    help="layered merge and/or gradient-weighted TV on the frame workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
