@@ -85,8 +85,16 @@ __global__ void seed_kernel(SeedArgs a)
     a.lo[view][(int64_t)y * a.W + x] = (uint16_t)lo;
 }
 
+// floor((a + b) / 2) of each 16-bit half: a & b + ((a ^ b) >> 1), the shift masked so
+// that no bit crosses from the high half into the low half
+__device__ __forceinline__ uint32_t avg_u16x2(uint32_t a, uint32_t b)
+{
+    return (a & b) + (((a ^ b) >> 1) & 0x7FFF7FFFu);
+}
+
 // Winner-take-all over each pixel's window, ties to the smallest disparity.  Four lanes
 // per pixel; the key (S << 16 | k) orders by energy, then by label.
+
 __global__ void wta_kernel(LevelArgs a)
 {
     const int view = blockIdx.z;
@@ -98,17 +106,25 @@ __global__ void wta_kernel(LevelArgs a)
     const ViewLevel &v = a.v[view];
     uint32_t best = 0xFFFFFFFFu;
     if (in) {
-        const uint16_t *s = v.S + i * a.Dws;
-        if (v.S2) {   // layered merge: the last layer's two passes, floor of the mean
-            const uint16_t *s2 = v.S2 + i * a.Dws;
-            for (int k = sub; k < a.Dw; k += 4) {
-                const uint32_t e = ((uint32_t)s[k] + (uint32_t)s2[k]) >> 1;
-                best = min(best, (e << 16) | (uint32_t)k);
+        // rows of Dws = 16k labels are 32k-byte aligned: each lane reads 8 labels at a
+        // time, the pixel's 4 lanes consecutive 16-byte chunks
+        const uint4 *row = (const uint4 *)(v.S + i * a.Dws);
+        const uint4 *row2 = v.S2 ? (const uint4 *)(v.S2 + i * a.Dws) : nullptr;
+        for (int c = sub; c < a.Dws / 8; c += 4) {
+            uint4 q = row[c];
+            if (row2) {   // layered merge: the last layer's two passes, floor of the mean
+                const uint4 q2 = row2[c];
+                q.x = avg_u16x2(q.x, q2.x);
+                q.y = avg_u16x2(q.y, q2.y);
+                q.z = avg_u16x2(q.z, q2.z);
+                q.w = avg_u16x2(q.w, q2.w);
             }
-        } else {
-            for (int k = sub; k < a.Dw; k += 4) {
-                const uint32_t key = ((uint32_t)s[k] << 16) | (uint32_t)k;
-                best = min(best, key);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = c * 8 + e;
+                const uint32_t val = (e & 1) ? (w[e >> 1] >> 16) : (w[e >> 1] & 0xFFFFu);
+                if (k < a.Dw) best = min(best, (val << 16) | (uint32_t)k);
             }
         }
     }
