@@ -1,0 +1,28 @@
+"""Host-side pieces of bench.py (no GPU): variant tables and algorithmic bytes."""
+import math
+
+import bench
+
+
+def test_gradient_table_is_rounded_exponential_within_p1():
+    t = bench.gradient_table(10, 16.0)
+    assert t.shape == (256,) and t[0] == 10 and (t >= 0).all() and (t <= 10).all()
+    assert all(t[g] == math.floor(10 * math.exp(-g / 16.0) + 0.5) for g in range(256))
+    assert (t[1:] <= t[:-1]).all()                     # non-increasing in the gradient
+
+
+def test_variant_names_keep_the_headline_for_the_plain_matcher():
+    assert bench.variant_names("plain") == (bench.METRIC, bench.WORKLOAD)
+    m, w = bench.variant_names("paper_gradient")
+    assert m.startswith(bench.METRIC[:-1]) and "layered merge" in m and "gradient" in w
+
+
+def test_algorithmic_bytes():
+    alg, nodes = bench.algorithmic_bytes()
+    assert nodes == 38_707_200                         # 1280x720, D=128, 3 scales, one view
+    px = sum(w * h for (w, h, _, _) in bench.level_geometry())
+    assert alg["aggregate"] == 2 * (3 * nodes + 2 * px)
+    lay, _ = bench.algorithmic_bytes(variant="paper")
+    # 8 paths = 4 layers: 6 B/node for the first, 12 B/node for each later one
+    assert lay["aggregate"] == 2 * 42 * nodes
+    assert lay["wta"] - alg["wta"] == 2 * 2 * nodes   # the last pair is read, not one S
