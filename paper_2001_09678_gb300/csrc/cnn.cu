@@ -229,11 +229,12 @@ __global__ void proposal_windows_kernel(const float *__restrict__ q, int Wq, int
 
 // Tensor-core form of conv3x3_kernel<32, bf16> (inference and training forward): an
 // implicit GEMM  out[p][co] = sum_k A[p][k] B[k][co]  with p = pixel, k = (tap, ci).
-// The block stages its input tile channels-last in shared memory (channel stride CP,
-// padded so that ldmatrix rows fall in distinct banks) and the weights as [co][tap][ci],
-// then every warp multiplies 32 pixels x 32 channels with mma.sync m16n8k16 (BF16 in,
-// FP32 accumulate).  Tile: 8 rows x 16 columns of pixels, 4 warps of 2 rows each.
-constexpr int kMmaRows = 8, kMmaCols = 16;
+// The block stages the weights once as [co][tap][ci] and, for each of its row tiles, the
+// input tile channels-last in shared memory (channel stride CP, padded so that ldmatrix
+// rows fall in distinct banks); every warp multiplies 32 pixels x 32 channels with
+// mma.sync m16n8k16 (BF16 in, FP32 accumulate).  Row tile: 8 rows x 16 columns of
+// pixels, 4 warps of 2 rows each; kMmaRowTiles tiles per block share the staged weights.
+constexpr int kMmaRows = 8, kMmaCols = 16, kMmaRowTiles = 2;
 
 __device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
                                         const void *p)
@@ -267,70 +268,87 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
     __nv_bfloat16 *xs = sm;                              // [TR][TC][CP]
     __nv_bfloat16 *ws = sm + TR * TC * CP;               // [32][9][CP]
     const int n = blockIdx.z;
-    const int x0 = blockIdx.x * kMmaCols, y0 = blockIdx.y * kMmaRows;
+    const int x0 = blockIdx.x * kMmaCols;
     const int64_t plane = (int64_t)H * W;
     const __nv_bfloat16 *src = in + (int64_t)n * Cin * plane;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    // consecutive threads read consecutive pixels (input) and taps (weights)
-    for (int i = threadIdx.x; i < TR * TC * CP; i += 128) {
-        const int px = i % TC, q = i / TC, py = q % TR, c = q / TR;
-        const int yy = y0 - 1 + py, xx = x0 - 1 + px;
-        xs[(py * TC + px) * CP + c] = (c < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                                          ? src[c * plane + (int64_t)yy * W + xx] : zero;
+    const int K16 = (Cin + 15) / 16 * 16;                // channels the k-steps cover
+    // weights: one (co, ci) pair per step, its 9 taps contiguous in global memory
+    for (int i = threadIdx.x; i < 32 * Cin; i += 128) {
+        const int co = i / Cin, c = i - co * Cin;
+        const __nv_bfloat16 *wr = w + (int64_t)i * 9;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) ws[(co * 9 + tap) * CP + c] = wr[tap];
     }
-    for (int i = threadIdx.x; i < 32 * 9 * CP; i += 128) {
-        const int tap = i % 9, q = i / 9, c = q % CP, co = q / CP;
-        ws[(co * 9 + tap) * CP + c] = c < Cin ? w[((int64_t)co * Cin + c) * 9 + tap] : zero;
-    }
-    __syncthreads();
+    // channels Cin .. K16-1 are zero in both operands (never rewritten below)
+    const int npad = K16 - Cin;
+    for (int i = threadIdx.x; i < 32 * 9 * npad; i += 128)
+        ws[(i / npad) * CP + Cin + i % npad] = zero;
+    for (int i = threadIdx.x; i < TR * TC * npad; i += 128)
+        xs[(i / npad) * CP + Cin + i % npad] = zero;
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float acc[2][4][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
     // ldmatrix row addresses: A rows = pixels of row (2*warp + mt), B rows = channels
     const int arow = lane & 15, acol = (lane >> 4) * 8;
     const int brow = lane & 7, bcol = ((lane >> 3) & 1) * 8;
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
-        for (int c0 = 0; c0 < CP - 8; c0 += 16) {
-            unsigned a[2][4];
+    const int g = lane >> 2, t = lane & 3;
+    for (int rt = 0; rt < kMmaRowTiles; ++rt) {
+        const int y0 = (blockIdx.y * kMmaRowTiles + rt) * kMmaRows;
+        if (y0 >= H) break;                              // uniform over the block
+        __syncthreads();                                 // the previous tile is consumed
+        // input tile, consecutive threads on consecutive pixels of a row
+        for (int i = threadIdx.x; i < TR * TC * Cin; i += 128) {
+            const int px = i % TC, q = i / TC, py = q % TR, c = q / TR;
+            const int yy = y0 - 1 + py, xx = x0 - 1 + px;
+            xs[(py * TC + px) * CP + c] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                                              ? src[c * plane + (int64_t)yy * W + xx] : zero;
+        }
+        __syncthreads();
+        float acc[2][4][4];
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int py = 2 * warp + mt + ky, px = arow + kx;
-                ldsm_x4(a[mt][0], a[mt][1], a[mt][2], a[mt][3], xs + (py * TC + px) * CP + c0 + acol);
-            }
+        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                unsigned b0, b1;
-                ldsm_x2(b0, b1, ws + ((nt * 8 + brow) * 9 + tap) * CP + c0 + bcol);
+            for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
-                    mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+            for (int c0 = 0; c0 < K16; c0 += 16) {
+                unsigned a[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int py = 2 * warp + mt + ky, px = arow + kx;
+                    ldsm_x4(a[mt][0], a[mt][1], a[mt][2], a[mt][3],
+                            xs + (py * TC + px) * CP + c0 + acol);
+                }
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    unsigned b0, b1;
+                    ldsm_x2(b0, b1, ws + ((nt * 8 + brow) * 9 + tap) * CP + c0 + bcol);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+                        mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                }
             }
         }
-    }
-    // accumulator layout: d0,d1 at (row g, cols 2t, 2t+1), d2,d3 at (row g+8, same cols)
-    const int g = lane >> 2, t = lane & 3;
+        // accumulator layout: d0,d1 at (row g, cols 2t, 2t+1), d2,d3 at (row g+8, same cols)
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int y = y0 + 2 * warp + mt;
+        for (int mt = 0; mt < 2; ++mt) {
+            const int y = y0 + 2 * warp + mt;
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int x = x0 + g + (e >= 2 ? 8 : 0);
-                const int co = nt * 8 + 2 * t + (e & 1);
-                if (x >= W || y >= H) continue;
-                float v = acc[mt][nt][e] + (b ? b[co] : 0.f);
-                if (relu) v = fmaxf(v, 0.f);
-                const int64_t o = ((int64_t)n * 32 + co) * plane + (int64_t)y * W + x;
-                if (out_f) out_f[o] = v;
-                if (out_bf) out_bf[o] = __float2bfloat16(v);
-            }
+                for (int e = 0; e < 4; ++e) {
+                    const int x = x0 + g + (e >= 2 ? 8 : 0);
+                    const int co = nt * 8 + 2 * t + (e & 1);
+                    if (x >= W || y >= H) continue;
+                    float v = acc[mt][nt][e] + (b ? b[co] : 0.f);
+                    if (relu) v = fmaxf(v, 0.f);
+                    const int64_t o = ((int64_t)n * 32 + co) * plane + (int64_t)y * W + x;
+                    if (out_f) out_f[o] = v;
+                    if (out_bf) out_bf[o] = __float2bfloat16(v);
+                }
+        }
     }
 }
 
@@ -367,7 +385,8 @@ void launch_conv3x3(const __nv_bfloat16 *in, int N, int Cin, int H, int W, const
     // channel stride: Cin rounded up to 16 (whole k-steps) plus 8 (bank spread)
     const int CP = (Cin + 15) / 16 * 16 + 8;
     const size_t smem = sizeof(__nv_bfloat16) * (size_t)CP * ((kMmaRows + 2) * (kMmaCols + 2) + 32 * 9);
-    dim3 grid((W + kMmaCols - 1) / kMmaCols, (H + kMmaRows - 1) / kMmaRows, N);
+    const int rows = kMmaRows * kMmaRowTiles;
+    dim3 grid((W + kMmaCols - 1) / kMmaCols, (H + rows - 1) / rows, N);
     cudaFuncSetAttribute(conv3x3_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     conv3x3_mma_kernel<<<grid, 128, smem, s>>>(in, Cin, CP, H, W, w, b, relu, out_bf, out_f);
 }

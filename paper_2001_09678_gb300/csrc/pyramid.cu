@@ -132,16 +132,25 @@ __global__ void wta_kernel(LevelArgs a)
     best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 2));
     const int lo = (in && v.lo) ? (int)v.lo[i] : 0;
     if (in && sub == 0) v.d[i] = (uint16_t)(lo + (best & 0xFFFFu));
-    if (a.edge) {
+    if (a.edge) {   // uniform over the grid: every thread of the block reaches the barriers
         // the minimum sits on the window's edge while the range continues beyond it
+        __shared__ unsigned counts[2];
+        if (threadIdx.x == 0) counts[0] = counts[1] = 0;
+        __syncthreads();
         const int k = (int)(best & 0xFFFFu);
         const bool hit = in && sub == 0 &&
                          ((k == 0 && lo > 0) || (k == a.Dw - 1 && lo + a.Dw < a.D));
         const unsigned nh = __popc(__ballot_sync(0xFFFFFFFFu, hit));
         const unsigned np = __popc(__ballot_sync(0xFFFFFFFFu, in && sub == 0));
         if ((threadIdx.x & 31) == 0 && np) {
-            atomicAdd(a.edge, (unsigned long long)nh);
-            atomicAdd(a.edge + 1, (unsigned long long)np);
+            atomicAdd(&counts[0], nh);
+            atomicAdd(&counts[1], np);
+        }
+        __syncthreads();
+        // one pair of global atomics per block instead of per warp
+        if (threadIdx.x == 0 && counts[1]) {
+            atomicAdd(a.edge, (unsigned long long)counts[0]);
+            atomicAdd(a.edge + 1, (unsigned long long)counts[1]);
         }
     }
 }
