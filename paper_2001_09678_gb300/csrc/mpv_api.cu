@@ -43,6 +43,8 @@ struct mpv_ctx {
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
+    std::vector<Graph> singles;   // single pairs (mpv_match), keyed like batches
+    bool single_graphs = true;
     std::map<uint64_t, Tuning> tuning;
     // learned proposal
     ProposalNet net;
@@ -74,6 +76,8 @@ mpv_status ensure_workspace(mpv_ctx *ctx, size_t bytes)
         cudaFree(ctx->ws);
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
+        for (auto &g : ctx->singles) cudaGraphExecDestroy(g.exec);   // they use the old one
+        ctx->singles.clear();
     }
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -171,6 +175,8 @@ void drop_graphs(mpv_ctx *ctx)
 {
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
+    for (auto &g : ctx->singles) cudaGraphExecDestroy(g.exec);
+    ctx->singles.clear();
 }
 
 // Autotuner: times the whole matcher on `job` once per candidate launch shape (after a
@@ -340,36 +346,91 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
 }
 
 // Enqueues one pair with the context's workspace and profiler.
+// The launches of one pair on stream s with the context's workspace (and, for the
+// learned proposal, the copy of the window-edge counters to pinned host memory).
+mpv_status enqueue_direct(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const StageSink *dbg,
+                          const Tuning &t, const Layout &L)
+{
+    StageHook hook{hook_begin, hook_end, ctx};
+    mpv_status r =
+        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t, &ctx->net, ctx->lut());
+    if (r == MPV_OK && ctx->p.proposal == MPV_PROPOSAL_LEARNED && !dbg) {
+        cudaMemcpyAsync(ctx->edge_host, (uint8_t *)ctx->ws + L.edge,
+                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        r = cuda_status(cudaGetLastError());
+    }
+    return r;
+}
+
+// Enqueues one pair with the context's workspace and profiler.  Without profiling or a
+// stage dump, the launches are captured once per signature (shape, parameters, buffers,
+// tuning, tables) into a CUDA graph on the context's capture stream and replayed on s.
 mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const StageSink *dbg)
 {
     if (check_grad(ctx) != MPV_OK) return MPV_ERR_INVALID_ARG;
     Geometry g;
     make_geometry(ctx->p, job.W, job.H, job.D, g);
     const Layout L = make_layout(g, views_needed(ctx->p, job, dbg), ctx->p);
-    const mpv_status st = ensure_workspace(ctx, L.total);
+    mpv_status st = ensure_workspace(ctx, L.total);
     if (st != MPV_OK) return st;
-    StageHook hook{hook_begin, hook_end, ctx};
     Tuning t;
     const auto it = ctx->tuning.find(shape_key(ctx->p, job.W, job.H, job.D));
     if (it != ctx->tuning.end()) t = it->second;
     const bool learned = ctx->p.proposal == MPV_PROPOSAL_LEARNED;
     if (learned && !ctx->net.layers) return MPV_ERR_INVALID_ARG;    // no weights loaded
-    mpv_status r =
-        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t, &ctx->net, ctx->lut());
-    if (r == MPV_OK && learned && !dbg) {
-        if (!ctx->edge_host) {
-            if (cudaMallocHost(&ctx->edge_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
-                cudaGetLastError();
-                return MPV_ERR_OOM;
-            }
-            ctx->edge_host[0] = ctx->edge_host[1] = 0;
+    if (learned && !dbg && !ctx->edge_host) {
+        if (cudaMallocHost(&ctx->edge_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return MPV_ERR_OOM;
         }
-        const Layout L = make_layout(g, views_needed(ctx->p, job, dbg), ctx->p);
-        cudaMemcpyAsync(ctx->edge_host, (uint8_t *)ctx->ws + L.edge,
-                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
-        r = cuda_status(cudaGetLastError());
+        ctx->edge_host[0] = ctx->edge_host[1] = 0;
     }
-    return r;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (dbg || ctx->profiling || !ctx->single_graphs ||
+        cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return enqueue_direct(ctx, job, s, dbg, t, L);
+    }
+    st = ensure_batch_streams(ctx);
+    if (st != MPV_OK) return st;
+    uint64_t sig = mix64(shape_key(ctx->p, job.W, job.H, job.D), (uint64_t)(uintptr_t)ctx->ws);
+    sig = mix64(sig, (uint64_t)(uintptr_t)job.left);
+    sig = mix64(sig, (uint64_t)(uintptr_t)job.right);
+    sig = mix64(sig, (uint64_t)(uintptr_t)job.disp);
+    sig = mix64(sig, (uint64_t)(uintptr_t)job.disp_right);
+    sig = mix64(sig, ((uint64_t)job.pitch << 32) | (uint32_t)job.disp_pitch);
+    sig = mix64(sig, (uint64_t)t.lanes);
+    sig = mix64(sig, (uint64_t)(uintptr_t)ctx->lut());
+    sig = mix64(sig, (uint64_t)(uintptr_t)ctx->net_mem);
+    sig = mix64(sig, (uint64_t)(uintptr_t)ctx->edge_host);
+    for (const auto &gr : ctx->singles)
+        if (gr.sig == sig) return cuda_status(cudaGraphLaunch(gr.exec, s));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return enqueue_direct(ctx, job, s, dbg, t, L);
+    }
+    const mpv_status est = enqueue_direct(ctx, job, ctx->cap, nullptr, t, L);
+    e = cudaStreamEndCapture(ctx->cap, &graph);
+    if (e != cudaSuccess || est != MPV_OK) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        return est != MPV_OK ? est : MPV_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MPV_ERR_CUDA;
+    }
+    if (ctx->singles.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(ctx->singles.front().exec);
+        ctx->singles.erase(ctx->singles.begin());
+    }
+    ctx->singles.push_back({sig, exec});
+    return cuda_status(cudaGraphLaunch(exec, s));
 }
 
 struct DeviceGuard {
