@@ -197,6 +197,25 @@ def replica_throughput(units_per_step, steps, world, slowest_ms):
     return world * steps * units_per_step / (slowest_ms / 1e3) / 1e6
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    kernel's source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("#") or "=" not in line:
+            continue
+        kv = dict(f.split("=", 1) for f in line.split())
+        src = os.path.join(ROOT, kv["source"])
+        if not os.path.exists(src):
+            return None
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return int(kv["bytes_per_launch"]) if h == kv["sha256_16"] else None
+    return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -333,7 +352,7 @@ def run_mine(args):
                          "peak_source": peak_kind,
                          "alg_bytes_per_step": alg[dom], "launches_per_step":
                              kern_launches / prof_steps,
-                         "traffic": None},
+                         "traffic": measured_traffic(dom) if args.variant == "plain" else None},
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
                     "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
                     "ms_per_step": round(1e3 * e2e_s / args.steps, 4),
