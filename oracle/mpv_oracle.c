@@ -795,3 +795,75 @@ int ora_match(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch,
     free(dl);
     return status;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Road detection (Section 3.5)                                                      */
+/* ------------------------------------------------------------------------------ */
+
+/* Eq. disp_map: the histogram of each image row over the disparities. */
+void ora_vdisparity(const uint16_t *U, int W, int H, int pitch, int D, uint32_t *Hx)
+{
+    memset(Hx, 0, sizeof(uint32_t) * (size_t)H * D);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int u = U[(int64_t)y * pitch + x];
+            if (u < D) Hx[(int64_t)y * D + u] += 1;
+        }
+}
+
+/* Eq. hy: the histogram of each image column; the equation prints the column index in
+ * the disparity's Kronecker delta, read as the disparity index (R21).                  */
+void ora_udisparity(const uint16_t *U, int W, int H, int pitch, int D, uint32_t *Hy)
+{
+    memset(Hy, 0, sizeof(uint32_t) * (size_t)W * D);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int u = U[(int64_t)y * pitch + x];
+            if (u < D) Hy[(int64_t)x * D + u] += 1;
+        }
+}
+
+/* Eqs. e and P_hat: e(i,j) = Hx(i,j) + max_{0 < j - j' < eta} e(i-1, j'), e(0,j) = Hx(0,j),
+ * a node without an admissible predecessor is unreachable (R22); the path runs over all
+ * D disparities and is read back from the best final row.                              */
+int64_t ora_road_profile(const uint32_t *Hx, int H, int D, int eta, int32_t *P)
+{
+    const int64_t NEG = -1;
+    int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)H * D);
+    int32_t *from = (int32_t *)malloc(sizeof(int32_t) * (size_t)H * D);
+    for (int j = 0; j < H; ++j) {
+        e[(int64_t)j * D + 0] = Hx[(int64_t)j * D + 0];
+        from[(int64_t)j * D + 0] = -1;
+    }
+    for (int i = 1; i < D; ++i)
+        for (int j = 0; j < H; ++j) {
+            int64_t best = NEG;
+            int arg = -1;
+            for (int jp = j - eta + 1; jp <= j - 1; ++jp) {
+                if (jp < 0) continue;
+                const int64_t v = e[(int64_t)jp * D + i - 1];
+                if (v > best) {
+                    best = v;
+                    arg = jp;
+                }
+            }
+            e[(int64_t)j * D + i] = best == NEG ? NEG : best + Hx[(int64_t)j * D + i];
+            from[(int64_t)j * D + i] = arg;
+        }
+    int64_t best = NEG;
+    int arg = -1;
+    for (int j = 0; j < H; ++j) {
+        const int64_t v = e[(int64_t)j * D + D - 1];
+        if (v > best) {
+            best = v;
+            arg = j;
+        }
+    }
+    for (int i = D - 1; i >= 0; --i) {
+        P[i] = arg;
+        if (arg >= 0) arg = from[(int64_t)arg * D + i];
+    }
+    free(e);
+    free(from);
+    return best;
+}

@@ -153,6 +153,23 @@ int ora_view_stage(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch
                    const ora_params *p, int level, int32_t *lo, int32_t *C, int64_t *S,
                    uint16_t *d);
 
+/* ------------------------------------------------------------------------------ */
+/* Road detection on the disparity map (Section 3.5: Eqs. disp_map, hy, e, P_hat)     */
+/* ------------------------------------------------------------------------------ */
+
+/* v-disparity: Hx[j*D + i] = number of pixels of row j whose disparity is i (i < D);
+ * other values (0xFFFF = rejected) are not counted.  U: W x H, rows `pitch` apart.   */
+void ora_vdisparity(const uint16_t *U, int W, int H, int pitch, int D, uint32_t *Hx);
+
+/* u-disparity: Hy[j*D + i] = number of pixels of column j whose disparity is i.      */
+void ora_udisparity(const uint16_t *U, int W, int H, int pitch, int D, uint32_t *Hy);
+
+/* Road profile: the row path j = P(i) over the disparities i = 0..D-1 that maximises
+ * sum_i Hx[P(i)][i] with 0 < P(i) - P(i-1) < eta.  Returns the maximum, or -1 (and P
+ * all -1) when no such path fits in H rows.  Ties go to the smaller row, at the end
+ * and at every predecessor.                                                          */
+int64_t ora_road_profile(const uint32_t *Hx, int H, int D, int eta, int32_t *P);
+
 #ifdef __cplusplus
 }
 #endif

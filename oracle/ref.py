@@ -107,6 +107,12 @@ def lib():
         for f in (L.ora_aggregate_grad, L.ora_aggregate_paper):
             f.argtypes = [i32p, i32p, i, i, i, i, C.c_int64, C.c_int64, i32p, u8p, i, i64p]
             f.restype = i
+        u32p = C.POINTER(C.c_uint32)
+        for f in (L.ora_vdisparity, L.ora_udisparity):
+            f.argtypes = [u16p, i, i, i, i, u32p]
+            f.restype = None
+        L.ora_road_profile.argtypes = [u32p, i, i, i, i32p]
+        L.ora_road_profile.restype = C.c_int64
         L.ora_wta.argtypes = [i64p, i32p, i, i, i, u16p]
         L.ora_wta.restype = None
         L.ora_downsample2.argtypes = [u8p, i, i, i, u8p, i]
@@ -366,3 +372,30 @@ def view_stage(I0, I1, p, level):
     if st != 0:
         raise ValueError(f"oracle view_stage failed: {st}")
     return lo, Cv, S, d
+
+
+def vdisparity(U, D):
+    """Row histograms over the disparities (ora_vdisparity): [H][D] uint32."""
+    U = np.ascontiguousarray(U, dtype=np.uint16)
+    H, W = U.shape
+    out = np.zeros((H, D), np.uint32)
+    lib().ora_vdisparity(_p(U, C.c_uint16), W, H, W, D, _p(out, C.c_uint32))
+    return out
+
+
+def udisparity(U, D):
+    """Column histograms over the disparities (ora_udisparity): [W][D] uint32."""
+    U = np.ascontiguousarray(U, dtype=np.uint16)
+    H, W = U.shape
+    out = np.zeros((W, D), np.uint32)
+    lib().ora_udisparity(_p(U, C.c_uint16), W, H, W, D, _p(out, C.c_uint32))
+    return out
+
+
+def road_profile(Hx, eta):
+    """(best sum, rows P[i] per disparity) of the road Viterbi (ora_road_profile)."""
+    Hx = np.ascontiguousarray(Hx, dtype=np.uint32)
+    H, D = Hx.shape
+    P = np.zeros(D, np.int32)
+    best = lib().ora_road_profile(_p(Hx, C.c_uint32), H, D, eta, _p(P, C.c_int32))
+    return best, P

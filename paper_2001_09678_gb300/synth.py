@@ -266,3 +266,28 @@ def mixed_batch_specs(counts=MIXED_BATCH, seed0=1000):
             out.append((seed0 + i, W, H, D))
             i += 1
     return out
+
+
+def road_disparity(W=1280, H=720, D=128, seed=0, horizon=300, rows_per_label=3,
+                   n_obstacles=6, outliers=0.02, invalid=0.05):
+    """A disparity map of a flat road seen by a level camera: rows below the horizon
+    carry the disparity floor((y - horizon) / rows_per_label) (clipped to D - 1), rows
+    above it a far background (0); n_obstacles fronto-parallel boxes standing on the road
+    (constant disparity, the road's at their bottom row); a share of outliers (uniform
+    disparities) and of rejected pixels (0xFFFF).  Returns uint16 [H][W]."""
+    ys = np.arange(H)[:, None].repeat(W, 1)
+    road = np.clip((ys - horizon) // rows_per_label, 0, D - 1)
+    U = np.where(ys >= horizon, road, 0).astype(np.int64)
+    box = uniform01(seed, 1, (n_obstacles, 4))
+    for k in range(n_obstacles):
+        bottom = int(horizon + 20 + box[k, 0] * (H - horizon - 21))
+        d = int(min(D - 1, (bottom - horizon) // rows_per_label))
+        h = int(10 + box[k, 1] * 3 * (d + 5))
+        w = int(10 + box[k, 2] * 4 * (d + 5))
+        x0 = int(box[k, 3] * max(1, W - w))
+        U[max(0, bottom - h):bottom, x0:x0 + w] = d
+    r = uniform01(seed, 2, (H, W))
+    noise = uniform_int(seed, 3, (H, W), 0, D)
+    U = np.where(r < outliers, noise, U)
+    U = np.where((r >= outliers) & (r < outliers + invalid), 0xFFFF, U)
+    return U.astype(np.uint16)
