@@ -46,7 +46,9 @@ VARIANTS = {          # merge mode, gradient weighting
     "paper": (1, False),
     "gradient": (0, True),
     "paper_gradient": (1, True),
+    "road": (0, False),          # plus road detection on every frame's disparity map
 }
+ROAD_ETA = 8
 
 
 def gradient_table(p1=PARAMS["p1"], sigma=GRAD_SIGMA):
@@ -60,6 +62,9 @@ def variant_names(variant):
     """Metric and workload strings of a variant (the plain matcher keeps the headline's)."""
     if variant == "plain":
         return METRIC, WORKLOAD
+    if variant == "road":
+        return (METRIC[:-1] + ", + road detection)",
+                WORKLOAD + f", + v/u-disparity and road profile (eta={ROAD_ETA})")
     merge, grad = VARIANTS[variant]
     tag = " + ".join(t for t, on in (("layered merge", merge), ("gradient TV", grad)) if on)
     return METRIC[:-1] + ", " + tag + ")", WORKLOAD + ", " + tag
@@ -257,9 +262,21 @@ def run_mine(args):
         mpv.mpv_set_gradient_penalty(ctx, gradient_table())
     metric, workload = variant_names(args.variant)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    road = args.variant == "road"
+    if road:
+        vd = torch.empty((H, D), dtype=torch.int32, device=dev)
+        ud = torch.empty((W, D), dtype=torch.int32, device=dev)
+        prof_r = torch.empty(D, dtype=torch.int32, device=dev)
+        en_r = torch.empty(1, dtype=torch.int64, device=dev)
+
+    def step():
+        mpv.mpv_match(ctx, left, right, disp, stream)
+        if road:
+            mpv.mpv_road_detect(ctx, disp, D, ROAD_ETA, vd, prof_r, en_r, udisp=ud,
+                                stream=stream)
 
     for _ in range(args.warmup):
-        mpv.mpv_match(ctx, left, right, disp, stream)
+        step()
     mpv.mpv_sync(ctx)
     mpv.mpv_profile_read(ctx)  # reset counters
 
@@ -278,7 +295,7 @@ def run_mine(args):
         for i in range(args.steps):
             flush.fill_(i & 0xFF)          # L2 flush between timed steps (not timed)
             starts[i].record(stream)
-            mpv.mpv_match(ctx, left, right, disp, stream)
+            step()
             ends[i].record(stream)
         torch.cuda.synchronize(dev)
         barrier()
@@ -296,6 +313,16 @@ def run_mine(args):
     torch.cuda.synchronize(dev)
     prof = mpv.mpv_profile_read(ctx)
     mpv.mpv_profile_enable(ctx, False)
+    road_ms = None
+    if road:   # the road stage alone, on the last disparity map
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        for _ in range(prof_steps):
+            mpv.mpv_road_detect(ctx, disp, D, ROAD_ETA, vd, prof_r, en_r, udisp=ud,
+                                stream=stream)
+        r1.record(stream)
+        torch.cuda.synchronize(dev)
+        road_ms = r0.elapsed_time(r1) / prof_steps
     total_ms = reduce_max(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
     value = replica_throughput(nominal_units(), args.steps, world, total_ms)
@@ -347,6 +374,7 @@ def run_mine(args):
             "evaluated_nodes_per_view": nodes,
             "stage_ms_per_step": {k: round(v / prof_steps, 4) for k, v in stage_ms.items()},
             "stage_profile": f"{prof_steps} further frames with per-stage events",
+            **({"road_ms_per_step": round(road_ms, 4)} if road_ms is not None else {}),
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "peak_source": peak_kind,

@@ -148,6 +148,25 @@ mpv_status mpv_autotune(mpv_ctx *ctx, const mpv_pair *pair, int32_t *lanes);
  * well); NULL switches the weighting off.  Applies to both merge modes.               */
 mpv_status mpv_set_gradient_penalty(mpv_ctx *ctx, const int32_t *slopes);
 
+/* Road detection on a disparity map (Section 3.5), asynchronous on cuda_stream; all
+ * pointers are device pointers.
+ *   disp: width x height uint16 disparities, rows disp_pitch elements apart; values not
+ *         below max_disparity (MPV_INVALID) are not counted.
+ *   vdisp (required, out): [height][max_disparity] uint32, the v-disparity (Eq. disp_map):
+ *         vdisp[j][i] = number of pixels of row j with disparity i.
+ *   udisp (optional, out): [width][max_disparity] uint32, the u-disparity (Eq. hy, read
+ *         with the disparity index): udisp[j][i] = pixels of column j with disparity i.
+ *   profile (out): [max_disparity] int32, the road's row P(i) for every disparity i: the
+ *         path maximising sum_i vdisp[P(i)][i] under 0 < P(i) - P(i-1) < eta (Eqs. e and
+ *         P_hat), ties to the smaller row; all -1 when no such path fits in the image.
+ *   energy (out): one int64, the maximum (-1 when no path fits).
+ * Limits: height <= 4096, max_disparity <= 1024, 2 <= eta <= 256; MPV_ERR_INVALID_ARG
+ * otherwise.  The context keeps a scratch buffer for tall inputs.                      */
+mpv_status mpv_road_detect(mpv_ctx *ctx, const uint16_t *disp, int32_t width, int32_t height,
+                           int32_t disp_pitch, int32_t max_disparity, int32_t eta,
+                           uint32_t *vdisp, uint32_t *udisp, int32_t *profile, int64_t *energy,
+                           void *cuda_stream);
+
 /* Loads the learned-proposal network (file written by paper_2001_09678_gb300/learn.py:
  * "MPVP", version 1, six layers of 3x3 convolutions, FP32 weights stored, converted to
  * BF16 on load).  With proposal = LEARNED (num_scales >= 2), a match computes the top

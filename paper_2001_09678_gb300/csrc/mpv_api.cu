@@ -54,6 +54,9 @@ struct mpv_ctx {
     bool grad_on = false;
     int32_t grad_host[256] = {};
     int *grad_dev = nullptr;
+    // road detection: steps back of the profile when they do not fit in shared memory
+    void *road_scratch = nullptr;
+    size_t road_scratch_bytes = 0;
 
     const int *lut() const { return grad_on ? grad_dev : nullptr; }
 };
@@ -730,6 +733,41 @@ mpv_status mpv_set_gradient_penalty(mpv_ctx *ctx, const int32_t *slopes)
     return MPV_OK;
 }
 
+mpv_status mpv_road_detect(mpv_ctx *ctx, const uint16_t *disp, int32_t width, int32_t height,
+                           int32_t disp_pitch, int32_t max_disparity, int32_t eta,
+                           uint32_t *vdisp, uint32_t *udisp, int32_t *profile, int64_t *energy,
+                           void *cuda_stream)
+{
+    if (!ctx || !disp || !vdisp || !profile || !energy || width < 1 || height < 1 ||
+        height > kRoadMaxRows || disp_pitch < width || max_disparity < 1 ||
+        max_disparity > 1024 || eta < 2 || eta > 256)
+        return MPV_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint8_t *scratch = nullptr;
+    if (!road_back_in_smem(height, max_disparity)) {
+        const size_t need = road_scratch_bytes(height, max_disparity);
+        if (ctx->road_scratch_bytes < need) {
+            if (ctx->road_scratch) {
+                cudaDeviceSynchronize();
+                cudaFree(ctx->road_scratch);
+            }
+            ctx->road_scratch = nullptr;
+            ctx->road_scratch_bytes = 0;
+            const cudaError_t e = cudaMalloc(&ctx->road_scratch, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return cuda_status(e);
+            }
+            ctx->road_scratch_bytes = need;
+        }
+        scratch = (uint8_t *)ctx->road_scratch;
+    }
+    launch_road(disp, width, height, disp_pitch, max_disparity, eta, vdisp, udisp, profile,
+                energy, scratch, s);
+    return cuda_status(cudaGetLastError());
+}
+
 mpv_status mpv_proposal_stats(const mpv_ctx *ctx, uint64_t *edge_hits, uint64_t *pixels)
 {
     if (!ctx) return MPV_ERR_INVALID_ARG;
@@ -882,6 +920,7 @@ void mpv_destroy(mpv_ctx *ctx)
         }
         if (ctx->net_mem) cudaFree(ctx->net_mem);
         if (ctx->grad_dev) cudaFree(ctx->grad_dev);
+        if (ctx->road_scratch) cudaFree(ctx->road_scratch);
         if (ctx->edge_host) cudaFreeHost(ctx->edge_host);
     }
     if (ctx->ws || ctx->stage) {

@@ -97,6 +97,16 @@ void launch_lr(const uint16_t *dL, const uint16_t *dRm, int W, int H, int tol, i
 // stage dumps: C (u8, stride Dws) -> u16 [.][Dw]; S (u16, stride Dws) -> u32 [.][Dw]
 void launch_unpack(const LevelArgs &a, int view, uint16_t *cost, uint32_t *sum, cudaStream_t s);
 
+// ---- road detection on the disparity map ------------------------------------------------
+
+// Hx [H][D] (required), Hy [W][D] (optional), profile P [D], best sum; scratch of
+// road_scratch_bytes(H, D) when !road_back_in_smem(H, D).
+void launch_road(const uint16_t *U, int W, int H, int pitch, int D, int eta, uint32_t *Hx,
+                 uint32_t *Hy, int32_t *P, int64_t *energy, uint8_t *scratch, cudaStream_t s);
+size_t road_scratch_bytes(int H, int D);
+bool road_back_in_smem(int H, int D);
+constexpr int kRoadMaxRows = 4096;
+
 // ---- learned proposal ---------------------------------------------------------------------
 
 constexpr int kProposalLayers = 6;

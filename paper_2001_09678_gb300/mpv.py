@@ -82,7 +82,7 @@ class mpv_pair(C.Structure):
 EXPORTS = [
     "mpv_default_params", "mpv_create", "mpv_set_params", "mpv_get_params", "mpv_match",
     "mpv_match_host", "mpv_match_batch", "mpv_load_proposal_weights", "mpv_sync",
-    "mpv_set_gradient_penalty",
+    "mpv_set_gradient_penalty", "mpv_road_detect",
     "mpv_workspace_bytes", "mpv_set_workspace_limit", "mpv_debug_stage", "mpv_level_info",
     "mpv_status_string", "mpv_destroy", "mpv_profile_enable", "mpv_profile_read",
     "mpv_match_noalloc", "mpv_autotune", "mpv_server_create", "mpv_server_add_camera",
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
     L.mpv_match_batch.argtypes = [ctx, C.POINTER(mpv_pair), i32, vp]
     L.mpv_load_proposal_weights.argtypes = [ctx, C.c_char_p]
     L.mpv_set_gradient_penalty.argtypes = [ctx, C.POINTER(C.c_int32)]
+    L.mpv_road_detect.argtypes = [ctx, vp, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp]
     L.mpv_sync.argtypes = [ctx]
     L.mpv_workspace_bytes.argtypes = [ctx, i32, i32, C.POINTER(C.c_size_t)]
     L.mpv_set_workspace_limit.argtypes = [ctx, C.c_size_t]
@@ -273,6 +274,16 @@ def mpv_set_gradient_penalty(ctx, slopes) -> None:
         raise ValueError("the gradient table has 256 entries")
     _check(load().mpv_set_gradient_penalty(ctx, a.ctypes.data_as(C.POINTER(C.c_int32))),
            "mpv_set_gradient_penalty")
+
+
+def mpv_road_detect(ctx, disp, max_disparity: int, eta: int, vdisp, profile, energy,
+                    udisp=None, stream=None) -> None:
+    """disp: [H][W] uint16 (int16 view) device tensor; vdisp [H][D] and udisp [W][D]
+    int32 tensors (uint32 counts), profile [D] int32, energy [1] int64."""
+    H, W = disp.shape[-2], disp.shape[-1]
+    _check(load().mpv_road_detect(ctx, _ptr(disp), W, H, disp.stride(-2), max_disparity, eta,
+                                  _ptr(vdisp), _ptr(udisp), _ptr(profile), _ptr(energy),
+                                  _stream(stream)), "mpv_road_detect")
 
 
 def mpv_load_proposal_weights(ctx, path: str) -> None:
