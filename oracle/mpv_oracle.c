@@ -336,9 +336,31 @@ static int64_t step_slope(int64_t p1, const int32_t *lut, const uint8_t *I0, int
     return lut[a > b ? a - b : b - a];
 }
 
+/* Section 3.4, read literally (f3): the top level split into block x block tiles, each
+ * tile its own MPV problem - a step whose predecessor lies in another tile starts the
+ * scan path anew.  block = 0: no split.                                               */
+static int crosses_block(int x, int y, int px, int py, int block)
+{
+    return block > 0 && (x / block != px / block || y / block != py / block);
+}
+
+static int path_pen_impl(const int64_t *Q, const int32_t *lo, int W, int H, int Dw, int dx,
+                         int dy, int64_t p1, int64_t T, const int32_t *lut, const uint8_t *I0,
+                         int pitch, int double_up, int normalize_out, int use_naive, int check,
+                         int block, int64_t *L);
+
 int ora_path_pen(const int64_t *Q, const int32_t *lo, int W, int H, int Dw, int dx, int dy,
                  int64_t p1, int64_t T, const int32_t *lut, const uint8_t *I0, int pitch,
                  int double_up, int normalize_out, int use_naive, int check, int64_t *L)
+{
+    return path_pen_impl(Q, lo, W, H, Dw, dx, dy, p1, T, lut, I0, pitch, double_up,
+                         normalize_out, use_naive, check, 0, L);
+}
+
+static int path_pen_impl(const int64_t *Q, const int32_t *lo, int W, int H, int Dw, int dx,
+                         int dy, int64_t p1, int64_t T, const int32_t *lut, const uint8_t *I0,
+                         int pitch, int double_up, int normalize_out, int use_naive, int check,
+                         int block, int64_t *L)
 {
     int status = 0;
     int64_t *M = (int64_t *)malloc(sizeof(int64_t) * (size_t)Dw);
@@ -354,7 +376,7 @@ int ora_path_pen(const int64_t *Q, const int32_t *lo, int W, int H, int Dw, int 
             const int64_t *q = Q + idx * Dw;
             int64_t *b = B + idx * Dw;
             const int px = x - dx, py = y - dy;
-            if (px < 0 || px >= W || py < 0 || py >= H) {
+            if (px < 0 || px >= W || py < 0 || py >= H || crosses_block(x, y, px, py, block)) {
                 for (int k = 0; k < Dw; ++k) b[k] = q[k];
             } else {
                 const int64_t pidx = (int64_t)py * W + px;
@@ -395,9 +417,20 @@ int ora_path_pen(const int64_t *Q, const int32_t *lo, int W, int H, int Dw, int 
     return status;
 }
 
+static int aggregate_grad_impl(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                               int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                               const uint8_t *I0, int pitch, int block, int64_t *S);
+
 int ora_aggregate_grad(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
                        int num_paths, int64_t p1, int64_t T, const int32_t *lut,
                        const uint8_t *I0, int pitch, int64_t *S)
+{
+    return aggregate_grad_impl(C, lo, W, H, Dw, num_paths, p1, T, lut, I0, pitch, 0, S);
+}
+
+static int aggregate_grad_impl(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                               int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                               const uint8_t *I0, int pitch, int block, int64_t *S)
 {
     const int64_t n = (int64_t)W * H * Dw;
     int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -411,8 +444,8 @@ int ora_aggregate_grad(const int32_t *C, const int32_t *lo, int W, int H, int Dw
     memset(S, 0, sizeof(int64_t) * (size_t)n);
     int status = 0;
     for (int r = 0; r < num_paths; ++r) {
-        if (ora_path_pen(Q, lo, W, H, Dw, ora_dirs[r][0], ora_dirs[r][1], p1, T, lut, I0, pitch,
-                         0, 0, 0, 0, L))
+        if (path_pen_impl(Q, lo, W, H, Dw, ora_dirs[r][0], ora_dirs[r][1], p1, T, lut, I0,
+                          pitch, 0, 0, 0, 0, block, L))
             status = -1;
         for (int64_t i = 0; i < n; ++i) S[i] += L[i];
     }
@@ -430,9 +463,29 @@ int ora_aggregate_grad(const int32_t *C, const int32_t *lo, int W, int H, int Dw
  * The left-to-right pass charges a jump from a smaller to a larger disparity twice
  * (reading: "twice penalty" doubles both the slope and the truncation).  The last
  * layer's merged energies are the output.                                            */
+static int aggregate_paper_impl(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                                int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                                const uint8_t *I0, int pitch, int block, int64_t *S);
+
 int ora_aggregate_paper(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
                         int num_paths, int64_t p1, int64_t T, const int32_t *lut,
                         const uint8_t *I0, int pitch, int64_t *S)
+{
+    return aggregate_paper_impl(C, lo, W, H, Dw, num_paths, p1, T, lut, I0, pitch, 0, S);
+}
+
+int ora_aggregate_blocks(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                         int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                         const uint8_t *I0, int pitch, int merge_mode, int block, int64_t *S)
+{
+    if (merge_mode == ORA_MERGE_PAPER)
+        return aggregate_paper_impl(C, lo, W, H, Dw, num_paths, p1, T, lut, I0, pitch, block, S);
+    return aggregate_grad_impl(C, lo, W, H, Dw, num_paths, p1, T, lut, I0, pitch, block, S);
+}
+
+static int aggregate_paper_impl(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                                int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                                const uint8_t *I0, int pitch, int block, int64_t *S)
 {
     const int64_t n = (int64_t)W * H * Dw;
     int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -450,10 +503,11 @@ int ora_aggregate_paper(const int32_t *C, const int32_t *lo, int W, int H, int D
     for (int layer = 0; layer < layers; ++layer) {
         const int *fw = ora_dirs[2 * layer], *bw = ora_dirs[2 * layer + 1];
         const int double_up = (fw[0] == 1 && fw[1] == 0);
-        if (ora_path_pen(Q, lo, W, H, Dw, fw[0], fw[1], p1, T, lut, I0, pitch, double_up, 1, 0,
-                         0, F))
+        if (path_pen_impl(Q, lo, W, H, Dw, fw[0], fw[1], p1, T, lut, I0, pitch, double_up, 1,
+                          0, 0, block, F))
             status = -1;
-        if (ora_path_pen(Q, lo, W, H, Dw, bw[0], bw[1], p1, T, lut, I0, pitch, 0, 1, 0, 0, B))
+        if (path_pen_impl(Q, lo, W, H, Dw, bw[0], bw[1], p1, T, lut, I0, pitch, 0, 1, 0, 0,
+                          block, B))
             status = -1;
         for (int64_t i = 0; i < n; ++i)
             Q[i] = layer == 0 ? min64(F[i], B[i]) : (F[i] + B[i]) / 2;
@@ -619,6 +673,7 @@ int ora_check_params(int W, int H, const ora_params *p)
     for (int l = 1; l < p->num_scales; ++l)
         if (p->block[l - 1] < 0 || p->block[l - 1] > 8) return -1;
     if (p->merge_mode != ORA_MERGE_SUM && p->merge_mode != ORA_MERGE_PAPER) return -1;
+    if (p->top_block < 0) return -1;
     if (p->grad_lut)
         for (int g = 0; g < 256; ++g)
             if (p->grad_lut[g] < 0 || p->grad_lut[g] > p->p1) return -1;
@@ -695,7 +750,10 @@ static int run_view(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitc
         if (l > 0) ora_seed(dprev, Wp, Hp, Wl, Hl, level_block(p, l), Dw, Dl, lo);
         ora_cost_volume(lv[l].I0, lv[l].I1, Wl, Hl, Wl, p->ssim_window, lo, Dw, C);
         int ag;
-        if (p->merge_mode == ORA_MERGE_PAPER)
+        if (l == 0 && p->top_block > 0)
+            ag = ora_aggregate_blocks(C, lo, Wl, Hl, Dw, p->num_paths, p->p1, T, p->grad_lut,
+                                      lv[l].I0, Wl, p->merge_mode, p->top_block, Sv);
+        else if (p->merge_mode == ORA_MERGE_PAPER)
             ag = ora_aggregate_paper(C, lo, Wl, Hl, Dw, p->num_paths, p->p1, T, p->grad_lut,
                                      lv[l].I0, Wl, Sv);
         else if (p->grad_lut)

@@ -39,6 +39,7 @@ typedef struct {
     int32_t lr_tol;         /* accepted |d_L - d_R| in pixels                      */
     int32_t merge_mode;     /* ORA_MERGE_SUM or ORA_MERGE_PAPER                    */
     const int32_t *grad_lut;/* NULL, or 256 jump slopes indexed by |I0(p) - I0(p-r)| */
+    int32_t top_block;      /* > 0: top level split into independent tiles of this side */
 } ora_params;
 
 /* Integer SSIM constants: round(C1 * n^2), round(C2 * n^2), n = N*N. */
@@ -110,6 +111,13 @@ int ora_aggregate_grad(const int32_t *C, const int32_t *lo, int W, int H, int Dw
 int ora_aggregate_paper(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
                         int num_paths, int64_t p1, int64_t T, const int32_t *lut,
                         const uint8_t *I0, int pitch, int64_t *S);
+
+/* Aggregation (merge_mode SUM or PAPER) with the image split into independent
+ * block x block tiles: a scan path restarts where it enters another tile (Section 3.4's
+ * "MPV for each block" at the top level).                                            */
+int ora_aggregate_blocks(const int32_t *C, const int32_t *lo, int W, int H, int Dw,
+                         int num_paths, int64_t p1, int64_t T, const int32_t *lut,
+                         const uint8_t *I0, int pitch, int merge_mode, int block, int64_t *S);
 
 /* Winner-take-all: d = lo + argmin_k S, ties to the smallest k. */
 void ora_wta(const int64_t *S, const int32_t *lo, int W, int H, int Dw, uint16_t *d);

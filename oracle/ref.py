@@ -34,6 +34,7 @@ class OraParams(C.Structure):
         ("lr_tol", C.c_int32),
         ("merge_mode", C.c_int32),
         ("grad_lut", C.POINTER(C.c_int32)),
+        ("top_block", C.c_int32),
     ]
 
 
@@ -52,7 +53,7 @@ def _lut(grad_lut):
 
 def params(max_disparity=32, num_scales=1, num_paths=4, p1=10, trunc=30, ssim_window=5,
            window=0, block=(0, 0, 0, 0), lr_check=1, lr_tol=1, merge_mode=MERGE_SUM,
-           grad_lut=None):
+           grad_lut=None, top_block=0):
     p = OraParams()
     p.max_disparity = max_disparity
     p.num_scales = num_scales
@@ -67,6 +68,7 @@ def params(max_disparity=32, num_scales=1, num_paths=4, p1=10, trunc=30, ssim_wi
     p.lr_check = lr_check
     p.lr_tol = lr_tol
     p.merge_mode = merge_mode
+    p.top_block = top_block
     p._lut_keep, ptr = _lut(grad_lut)   # the table must outlive the struct's pointer
     if ptr is not None:
         p.grad_lut = ptr
@@ -107,6 +109,9 @@ def lib():
         for f in (L.ora_aggregate_grad, L.ora_aggregate_paper):
             f.argtypes = [i32p, i32p, i, i, i, i, C.c_int64, C.c_int64, i32p, u8p, i, i64p]
             f.restype = i
+        L.ora_aggregate_blocks.argtypes = [i32p, i32p, i, i, i, i, C.c_int64, C.c_int64, i32p,
+                                           u8p, i, i, i, i64p]
+        L.ora_aggregate_blocks.restype = i
         u32p = C.POINTER(C.c_uint32)
         for f in (L.ora_vdisparity, L.ora_udisparity):
             f.argtypes = [u16p, i, i, i, i, u32p]
@@ -267,6 +272,21 @@ def _aggregate_pen(fn, Cv, num_paths, p1, T, lo, grad_lut, I0):
 def aggregate_grad(Cv, num_paths, p1, T, lo=None, grad_lut=None, I0=None):
     """Sum of bounded passes with gradient-weighted slopes (ora_aggregate_grad)."""
     return _aggregate_pen(lib().ora_aggregate_grad, Cv, num_paths, p1, T, lo, grad_lut, I0)
+
+
+def aggregate_blocks(Cv, num_paths, p1, T, block, merge_mode=MERGE_SUM, lo=None,
+                     grad_lut=None, I0=None):
+    """Aggregation with the image split into independent block x block tiles."""
+    Cv = np.ascontiguousarray(Cv, dtype=np.int32)
+    H, W, Dw = Cv.shape
+    S = np.zeros((H, W, Dw), np.int64)
+    lo, lop = _opt_lo(lo)
+    lut, lutp = _lut(grad_lut)
+    img, imgp = _opt_img(I0, grad_lut)
+    st = lib().ora_aggregate_blocks(_p(Cv, C.c_int32), lop, W, H, Dw, num_paths, p1, T, lutp,
+                                    imgp, W, merge_mode, block, _p(S, C.c_int64))
+    assert st == 0
+    return S
 
 
 def aggregate_paper(Cv, num_paths, p1, T, lo=None, grad_lut=None, I0=None):
