@@ -82,6 +82,9 @@ typedef struct {
     int32_t lr_tol;         /* accepted |d_L - d_R| in pixels (default 1)                  */
     int32_t merge_mode;     /* MPV_MERGE_SUM or MPV_MERGE_PAPER                             */
     int32_t proposal;       /* MPV_PROPOSAL_PYRAMID or MPV_PROPOSAL_LEARNED                */
+    int32_t top_block;      /* > 0: the top pyramid level is split into independent tiles  */
+                            /* of top_block x top_block pixels, MPV per tile (Section 3.4, */
+                            /* read literally); 0 (default): the whole top level           */
 } mpv_params;
 
 /* One stereo pair of a batch.  All pointers are device pointers. */

@@ -114,7 +114,9 @@ __device__ __forceinline__ int path_length(int dx, int dy, int W, int H, int x0,
 // RM (ceil(T/p1) - 1 <= RM) the stencil min over |d| <= RM plus the cap min_v A(v) + T
 // is the full-connectivity minimum.  WIN: the level has per-pixel windows, and the
 // predecessor is re-indexed into the current window through shared memory every step.
-template <int G, int KW, int RM, bool WIN>
+// BLK: the level is split into independent block_cut x block_cut tiles (a scan path
+// restarts where it enters a new tile); counters track the steps to the next tile edge.
+template <int G, int KW, int RM, bool WIN, bool BLK>
 __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
 {
     constexpr int kG = G;                    // lanes per scan path
@@ -199,6 +201,15 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
 #pragma unroll
     for (int i = 0; i < KW; ++i) A[i] = INF2;   // no predecessor: L = C at the first pixel
     int prev_lo = -1;
+    // steps to the next tile edge in x and in y (BLK)
+    const int B = a.block_cut;
+    int cx = 0x7FFFFFFF, cy = 0x7FFFFFFF;
+    if (BLK) {
+        if (dx > 0) cx = B - x0 % B;
+        if (dx < 0) cx = x0 % B + 1;
+        if (dy > 0) cy = B - y0 % B;
+        if (dy < 0) cy = y0 % B + 1;
+    }
 
     for (int t0 = 0; t0 < nmax; t0 += PF) {
 #pragma unroll
@@ -216,6 +227,15 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
             const int cur_lo = (int)lq[u];
             issue(t + PF, u);
 
+            if (BLK && t > 0) {   // entering a new tile: the path starts again here
+                const bool cut = --cx == 0 || --cy == 0;
+                if (cx == 0) cx = B;
+                if (cy == 0) cy = B;
+                if (cut) {
+#pragma unroll
+                    for (int i = 0; i < KW; ++i) A[i] = INF2;
+                }
+            }
             // minimum of the predecessor over the path's lanes, in both halves
             uint32_t m2 = A[0];
 #pragma unroll
@@ -300,25 +320,29 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
     }
 }
 
-template <int G, int KW, int RM, bool WIN>
+template <int G, int KW, int RM, bool WIN, bool BLK>
 void launch_stencil(const LevelArgs &a, cudaStream_t s)
 {
     const int maxp = a.W + a.H - 1;
     const int per_block = kStencilWarps * (32 / G);
     dim3 grid((maxp + per_block - 1) / per_block, a.npaths, a.nviews);
-    agg_stencil<G, KW, RM, WIN><<<grid, kStencilWarps * 32, 0, s>>>(a);
+    agg_stencil<G, KW, RM, WIN, BLK><<<grid, kStencilWarps * 32, 0, s>>>(a);
 }
 
+// windows (pyramid levels below the top) and tiles (the top level only) never meet
 template <int G, int KW>
 void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
 {
     const bool win = a.v[0].lo != nullptr;
+    const bool blk = a.block_cut > 0;
     if (a.radius <= 2) {
-        if (win) launch_stencil<G, KW, 2, true>(a, s);
-        else launch_stencil<G, KW, 2, false>(a, s);
+        if (win) launch_stencil<G, KW, 2, true, false>(a, s);
+        else if (blk) launch_stencil<G, KW, 2, false, true>(a, s);
+        else launch_stencil<G, KW, 2, false, false>(a, s);
     } else {
-        if (win) launch_stencil<G, KW, 4, true>(a, s);
-        else launch_stencil<G, KW, 4, false>(a, s);
+        if (win) launch_stencil<G, KW, 4, true, false>(a, s);
+        else if (blk) launch_stencil<G, KW, 4, false, true>(a, s);
+        else launch_stencil<G, KW, 4, false, false>(a, s);
     }
 }
 
@@ -393,6 +417,10 @@ __global__ void __launch_bounds__(kScanWarps * 32) agg_general(LevelArgs a, Merg
             c[t] = v;
         }
         const int cur_i = m.lut ? (int)V.I0[(int64_t)y * V.pitch0 + x] : 0;
+        // entering a new tile of a split level: the path starts again here
+        if (a.block_cut > 0 && !first &&
+            (x / a.block_cut != (x - dx) / a.block_cut || y / a.block_cut != (y - dy) / a.block_cut))
+            first = true;
         int L[K];
         if (first) {
 #pragma unroll

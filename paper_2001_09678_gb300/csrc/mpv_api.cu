@@ -471,6 +471,7 @@ mpv_status mpv_default_params(mpv_params *p)
     p->lr_tol = 1;
     p->merge_mode = MPV_MERGE_SUM;
     p->proposal = MPV_PROPOSAL_PYRAMID;
+    p->top_block = 0;
     return MPV_OK;
 }
 

@@ -52,6 +52,7 @@ bool params_valid(const mpv_params &p)
     if (p.lr_check != 0 && p.lr_check != 1) return false;
     if (p.merge_mode != MPV_MERGE_SUM && p.merge_mode != MPV_MERGE_PAPER) return false;
     if (p.proposal != MPV_PROPOSAL_PYRAMID && p.proposal != MPV_PROPOSAL_LEARNED) return false;
+    if (p.top_block < 0) return false;
     for (int i = 0; i < 4; ++i)
         if (p.block[i] < 0 || p.block[i] > 8) return false;
     return true;
@@ -249,6 +250,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
         a.radius = a.p1 > 0 ? (int)((Teff + a.p1 - 1) / a.p1) - 1 : 0;
         a.npaths = p.num_paths;
         a.lanes = tune.lanes;
+        a.block_cut = l == 0 ? p.top_block : 0;
         for (int v = 0; v < nviews; ++v) {
             ViewLevel &vl = a.v[v];
             vl.I0 = I0[v][l];

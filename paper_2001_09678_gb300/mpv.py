@@ -51,6 +51,7 @@ class mpv_params(C.Structure):
         ("lr_tol", C.c_int32),
         ("merge_mode", C.c_int32),
         ("proposal", C.c_int32),
+        ("top_block", C.c_int32),
     ]
 
 

@@ -1,5 +1,6 @@
-"""The paper's layered merge (Section 3.2) and the gradient-weighted TV penalty (Eq. EU) on
-the GPU, against the CPU oracle: bit-exact disparities, right-view maps and stage volumes.
+"""The paper's layered merge (Section 3.2), the gradient-weighted TV penalty (Eq. EU) and the
+top level split into independent tiles (Section 3.4) on the GPU, against the CPU oracle:
+bit-exact disparities, right-view maps and stage volumes.
 """
 import numpy as np
 import pytest
@@ -11,7 +12,7 @@ from oracle import ref  # noqa: E402
 from paper_2001_09678_gb300 import synth  # noqa: E402
 
 ORA_KEYS = ("max_disparity", "num_scales", "num_paths", "p1", "trunc", "ssim_window", "window",
-            "block", "lr_check", "lr_tol", "merge_mode")
+            "block", "lr_check", "lr_tol", "merge_mode", "top_block")
 
 
 @pytest.fixture(scope="module")
@@ -92,6 +93,20 @@ CASES = {
     "paper_grad_s3": (lambda: synth.slanted_pair(224, 128, seed=49, d_max=56)[:2],
                       dict(max_disparity=64, num_scales=3, num_paths=8, merge_mode=PAPER),
                       exp_table(10, 16)),
+    # the top level split into independent tiles (Section 3.4 read literally)
+    "tiles_s3_b16": (lambda: synth.slanted_pair(256, 160, seed=70, d_max=60)[:2],
+                     dict(max_disparity=64, num_scales=3, num_paths=8, top_block=16), None),
+    "tiles_s1_b24_p4": (lambda: synth.bands_pair(320, 240, seed=71)[:2],
+                        dict(max_disparity=32, num_scales=1, num_paths=4, top_block=24), None),
+    "tiles_radius4_b7": (lambda: synth.slanted_pair(192, 96, seed=72, d_max=40)[:2],
+                         dict(max_disparity=48, num_scales=2, num_paths=8, p1=10, trunc=45,
+                              top_block=7), None),
+    "tiles_general_notrunc": (lambda: synth.bands_pair(150, 70, seed=73)[:2],
+                              dict(max_disparity=40, num_scales=1, num_paths=8, p1=3,
+                                   trunc=ref.NO_TRUNC, top_block=20), None),
+    "tiles_paper_grad": (lambda: synth.slanted_pair(224, 128, seed=74, d_max=56)[:2],
+                         dict(max_disparity=64, num_scales=3, num_paths=8, merge_mode=PAPER,
+                              top_block=12), exp_table(10, 16)),
 }
 
 
@@ -107,11 +122,12 @@ def test_variant_disparity_bit_exact(mpv, name):
 
 @pytest.mark.parametrize("view", [0, 1])
 @pytest.mark.parametrize("level", [0, 2])
-@pytest.mark.parametrize("variant", ["paper", "grad", "paper_grad"])
+@pytest.mark.parametrize("variant", ["paper", "grad", "paper_grad", "tiles"])
 def test_variant_stage_volumes_bit_exact(mpv, view, level, variant):
     L, R, _ = synth.bands_pair(123, 77, seed=50)
     kw = dict(max_disparity=48, num_scales=3, num_paths=8, window=12,
-              merge_mode=PAPER if variant.startswith("paper") else 0)
+              merge_mode=PAPER if variant.startswith("paper") else 0,
+              top_block=5 if variant == "tiles" else 0)
     lut = exp_table(10, 8) if variant.endswith("grad") else None
     p = ora_params(lut, **kw)
     I0, I1 = (L, R) if view == 0 else (np.ascontiguousarray(R[:, ::-1]),
