@@ -41,14 +41,17 @@ CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 L2_FLUSH_BYTES = 256 << 20
 GRAD_SIGMA = 16.0
-VARIANTS = {          # merge mode, gradient weighting
-    "plain": (0, False),
-    "paper": (1, False),
-    "gradient": (0, True),
-    "paper_gradient": (1, True),
-    "road": (0, False),          # plus road detection on every frame's disparity map
+VARIANTS = {          # merge mode, gradient weighting, learned window (0: pyramid)
+    "plain": (0, False, 0),
+    "paper": (1, False, 0),
+    "gradient": (0, True, 0),
+    "paper_gradient": (1, True, 0),
+    "road": (0, False, 0),       # plus road detection on every frame's disparity map
+    "learned": (0, False, 17),   # learned window proposal, centre +- 8
+    "learned16": (0, False, 16),  # learned window proposal, one 16-label stride
 }
 ROAD_ETA = 8
+WEIGHTS = os.path.join(ROOT, "paper_2001_09678_gb300", "weights", "proposal_d128_s3.bin")
 
 
 def gradient_table(p1=PARAMS["p1"], sigma=GRAD_SIGMA):
@@ -65,7 +68,12 @@ def variant_names(variant):
     if variant == "road":
         return (METRIC[:-1] + ", + road detection)",
                 WORKLOAD + f", + v/u-disparity and road profile (eta={ROAD_ETA})")
-    merge, grad = VARIANTS[variant]
+    merge, grad, lw = VARIANTS[variant]
+    if lw:
+        tag = f"learned proposal, {lw}-label finest window"
+        return (METRIC.replace("3-scale MPV", "learned-proposal MPV")[:-1] + f", window {lw})",
+                WORKLOAD + f", learned window proposal (6-layer CNN at the top level, "
+                           f"finest-level window {lw}, intermediate level skipped)")
     tag = " + ".join(t for t, on in (("layered merge", merge), ("gradient TV", grad)) if on)
     return METRIC[:-1] + ", " + tag + ")", WORKLOAD + ", " + tag
 
@@ -107,11 +115,17 @@ def algorithmic_bytes(views=2, variant="plain"):
     that (2 B/node) and writes the uint16 map.  The layered merge stores each pass
     (2 B/node per direction) and reads the previous layer's pair (4 B/node per
     direction; the first layer reads the cost bytes), and its WTA reads the last pair."""
-    merge, grad = VARIANTS[variant]
+    merge, grad, lw = VARIANTS[variant]
     layers = PARAMS["num_paths"] // 2
     cost = agg = wta = 0
     nodes = 0
-    for (w, h, Dl, Dw) in level_geometry():
+    levels = level_geometry()
+    if lw:   # the top level's cost feeds the network; the finest level searches lw labels
+        (w0, h0, _, D0), (w2, h2, D2, _) = levels[0], levels[-1]
+        cost += views * (w0 * h0 * D0 + 2 * w0 * h0)
+        levels = [(w2, h2, D2, lw)]
+        nodes = w0 * h0 * D0
+    for (w, h, Dl, Dw) in levels:
         n = w * h * Dw
         nodes += n
         cost += views * (n + 2 * w * h)
@@ -256,10 +270,13 @@ def run_mine(args):
     disp = torch.empty((H, W), dtype=torch.int16, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = mpv.mpv_create(local)
-    merge, grad = VARIANTS[args.variant]
-    mpv.mpv_set_params(ctx, mpv.mpv_default_params(merge_mode=merge, **PARAMS))
+    merge, grad, lw = VARIANTS[args.variant]
+    extra = dict(proposal=mpv.MPV_PROPOSAL_LEARNED, window=lw) if lw else {}
+    mpv.mpv_set_params(ctx, mpv.mpv_default_params(merge_mode=merge, **extra, **PARAMS))
     if grad:
         mpv.mpv_set_gradient_penalty(ctx, gradient_table())
+    if lw:
+        mpv.mpv_load_proposal_weights(ctx, WEIGHTS)
     metric, workload = variant_names(args.variant)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     road = args.variant == "road"
@@ -394,7 +411,8 @@ def run_mine(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not lw:
+        # (the oracle has no network: the learned variants report no CPU baseline)
         out["cpu_baseline"] = cpu_baseline_full(L, R, args.variant)
     if out is not None:
         print(json.dumps(out), flush=True)
@@ -406,7 +424,7 @@ def run_mine(args):
 
 def _ora_params(variant="plain"):
     from oracle import ref
-    merge, grad = VARIANTS[variant]
+    merge, grad, _ = VARIANTS[variant]
     return ref.params(window=0, block=(0, 0, 0, 0), merge_mode=merge,
                       grad_lut=gradient_table() if grad else None, **PARAMS)
 
@@ -427,6 +445,10 @@ def cpu_baseline_full(L, R, variant="plain"):
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if VARIANTS[args.variant][2]:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no network: "
+                          "the learned window proposal has no CPU reference"}), flush=True)
         return
     from oracle import ref
     from paper_2001_09678_gb300 import synth
