@@ -45,10 +45,18 @@ __global__ void __launch_bounds__(kHistThreads) udisp_kernel(const uint16_t *__r
     for (int i = threadIdx.x; i < kUCols * D; i += kHistThreads) hist[i] = 0;
     __syncthreads();
     const int x = x0 + lane;
+    constexpr int kRows = kHistThreads / 32, kBatch = 8;
     if (x < W)
-        for (int y = warp; y < H; y += kHistThreads / 32) {
-            const int u = U[(int64_t)y * pitch + x];
-            if (u < D) atomicAdd(&hist[lane * D + u], 1u);
+        for (int y0 = warp; y0 < H; y0 += kRows * kBatch) {
+            int u[kBatch];   // the batch's loads are issued before its shared atomics
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b) {
+                const int y = y0 + b * kRows;
+                u[b] = y < H ? U[(int64_t)y * pitch + x] : D;
+            }
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b)
+                if (u[b] < D) atomicAdd(&hist[lane * D + u[b]], 1u);
         }
     __syncthreads();
     const int ncols = min(kUCols, W - x0);
@@ -61,11 +69,11 @@ __global__ void __launch_bounds__(kHistThreads) udisp_kernel(const uint16_t *__r
 // shared memory when it fits (SMEM_BACK) or in the global scratch otherwise.  The
 // histogram is staged kRoadChunk disparities at a time, transposed, so that each step
 // reads shared memory only.
-constexpr int kRoadChunk = 8;
+constexpr int kRoadChunk = 32;          // at most; fewer when the rows are many
 
 template <bool SMEM_BACK>
 __global__ void __launch_bounds__(kRoadThreads) road_kernel(const uint32_t *__restrict__ Hx,
-                                                            int H, int D, int eta,
+                                                            int H, int D, int eta, int chunk_n,
                                                             uint8_t *__restrict__ back_g,
                                                             int32_t *__restrict__ P,
                                                             int64_t *__restrict__ energy)
@@ -73,16 +81,22 @@ __global__ void __launch_bounds__(kRoadThreads) road_kernel(const uint32_t *__re
     extern __shared__ __align__(16) unsigned char sm[];
     int32_t *e0 = (int32_t *)sm;
     int32_t *e1 = e0 + H;
-    uint32_t *chunk = (uint32_t *)(e1 + H);            // [kRoadChunk][H]
-    uint8_t *back = SMEM_BACK ? (uint8_t *)(chunk + kRoadChunk * H) : back_g;
+    uint32_t *chunk = (uint32_t *)(e1 + H);            // [chunk_n][H]
+    uint8_t *back = SMEM_BACK ? (uint8_t *)(chunk + chunk_n * H) : back_g;
     __shared__ unsigned long long red[kRoadThreads / 32];
     int32_t *prev = e0, *cur = e1;
-    for (int i0 = 0; i0 < D; i0 += kRoadChunk) {
-        const int nc = min(kRoadChunk, D - i0);
+    for (int i0 = 0; i0 < D; i0 += chunk_n) {
+        const int nc = min(chunk_n, D - i0);
         __syncthreads();                                // the previous chunk is consumed
-        for (int idx = threadIdx.x; idx < H * nc; idx += kRoadThreads) {
-            const int j = idx / nc, c = idx - j * nc;
-            chunk[c * H + j] = Hx[(int64_t)j * D + i0 + c];
+        // a thread's loads of a row are issued together, then stored transposed
+        for (int j = threadIdx.x; j < H; j += kRoadThreads) {
+            uint32_t v[kRoadChunk];
+#pragma unroll
+            for (int c = 0; c < kRoadChunk; ++c)
+                if (c < nc) v[c] = Hx[(int64_t)j * D + i0 + c];
+#pragma unroll
+            for (int c = 0; c < kRoadChunk; ++c)
+                if (c < nc) chunk[c * H + j] = v[c];
         }
         __syncthreads();
         for (int c = 0; c < nc; ++c) {
@@ -141,9 +155,15 @@ __global__ void __launch_bounds__(kRoadThreads) road_kernel(const uint32_t *__re
 
 size_t road_scratch_bytes(int H, int D) { return (size_t)H * D; }
 
-// shared memory of the road kernel: e (two rows of H), the staged chunk, and the steps
-// back when they fit
-size_t road_smem_base(int H) { return (8 + 4 * (size_t)kRoadChunk) * (size_t)H; }
+// shared memory of the road kernel: e (two rows of H), the staged chunk of disparities
+// (as many as fit in 96 KB, up to 32), and the steps back when they fit
+int road_chunk(int H)
+{
+    int c = kRoadChunk;
+    while (c > 1 && (size_t)4 * c * H > 96 * 1024) c >>= 1;
+    return c;
+}
+size_t road_smem_base(int H) { return (8 + 4 * (size_t)road_chunk(H)) * (size_t)H; }
 bool road_back_in_smem(int H, int D) { return road_smem_base(H) + (size_t)H * D <= 200 * 1024; }
 
 void launch_road(const uint16_t *U, int W, int H, int pitch, int D, int eta, uint32_t *Hx,
@@ -159,12 +179,14 @@ void launch_road(const uint16_t *U, int W, int H, int pitch, int D, int eta, uin
         const size_t smem = road_smem_base(H) + (size_t)H * D;
         cudaFuncSetAttribute(road_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        road_kernel<true><<<1, kRoadThreads, smem, s>>>(Hx, H, D, eta, nullptr, P, energy);
+        road_kernel<true><<<1, kRoadThreads, smem, s>>>(Hx, H, D, eta, road_chunk(H), nullptr, P,
+                                                         energy);
     } else {
         const size_t smem = road_smem_base(H);
         cudaFuncSetAttribute(road_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        road_kernel<false><<<1, kRoadThreads, smem, s>>>(Hx, H, D, eta, scratch, P, energy);
+        road_kernel<false><<<1, kRoadThreads, smem, s>>>(Hx, H, D, eta, road_chunk(H), scratch, P,
+                                                          energy);
     }
 }
 
