@@ -114,7 +114,10 @@ mpv_status mpv_get_params(const mpv_ctx *ctx, mpv_params *p);
 /* Disparity map of one rectified pair (left view), device pointers, asynchronous.
  * Requirements: width, height >= N; 1 <= D <= min(width, 1024); the top pyramid level
  * at least N x N; pitch >= width; disp_pitch >= width; and the bound on summed
- * energies num_paths * (255 + min(T, p1 * (D - 1))) < 65535.                          */
+ * energies num_paths * (255 + min(T, p1 * (D - 1))) < 65535.
+ * The launches of a pair are captured once per signature (sizes, buffers, parameters,
+ * tables) into a CUDA graph that later calls replay; with MPV_NO_GRAPHS set in the
+ * environment, or while profiling or dumping stages, they are launched directly.      */
 mpv_status mpv_match(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
                      int32_t width, int32_t height, int32_t pitch, uint16_t *disp,
                      int32_t disp_pitch, void *cuda_stream);
@@ -244,6 +247,13 @@ typedef struct {
 
 mpv_status mpv_server_create(int device, const mpv_params *params, size_t hbm_budget,
                              int32_t max_inflight, mpv_server **out);
+/* Learned window proposal for the cameras of a server: weights file as for
+ * mpv_load_proposal_weights.  A camera whose range fits the network (2 + top-level range
+ * input channels) matches with the learned proposal, the others with the pyramid; NULL
+ * returns every camera to the pyramid.  Applies to cameras made resident afterwards
+ * (call before the first submit).                                                    */
+mpv_status mpv_server_set_proposal(mpv_server *server, const char *weights_path);
+
 /* Registers a camera's frame geometry and range (validated as for mpv_match). */
 mpv_status mpv_server_add_camera(mpv_server *srv, int32_t camera, int32_t width,
                                  int32_t height, int32_t max_disparity);

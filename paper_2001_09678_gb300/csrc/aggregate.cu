@@ -228,7 +228,9 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
             issue(t + PF, u);
 
             if (BLK && t > 0) {   // entering a new tile: the path starts again here
-                const bool cut = --cx == 0 || --cy == 0;
+                --cx;
+                --cy;
+                const bool cut = cx == 0 || cy == 0;
                 if (cx == 0) cx = B;
                 if (cy == 0) cy = B;
                 if (cut) {

@@ -44,7 +44,9 @@ struct mpv_ctx {
     };
     std::vector<Graph> graphs;
     std::vector<Graph> singles;   // single pairs (mpv_match), keyed like batches
-    bool single_graphs = true;
+    // MPV_NO_GRAPHS set in the environment: single pairs launch directly (profilers that
+    // replay graph nodes one by one)
+    bool single_graphs = std::getenv("MPV_NO_GRAPHS") == nullptr;
     std::map<uint64_t, Tuning> tuning;
     // learned proposal
     ProposalNet net;
@@ -60,6 +62,19 @@ struct mpv_ctx {
 
     const int *lut() const { return grad_on ? grad_dev : nullptr; }
 };
+
+namespace mpv {
+
+// The loaded network takes the top level of range D under the context's parameters.
+bool proposal_fits(const mpv_ctx *ctx, int D)
+{
+    const int S = ctx->p.num_scales;
+    if (!ctx->net.layers || S < 2) return false;
+    const int top = (D + (1 << (S - 1)) - 1) >> (S - 1);
+    return ctx->net.cin[0] == 2 + top;
+}
+
+}  // namespace mpv
 
 namespace {
 

@@ -183,6 +183,9 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *worksp
                         cudaStream_t s, const StageHook *hook, const StageSink *dbg,
                         const Tuning &tune = Tuning(), const ProposalNet *net = nullptr,
                         const int *grad_lut = nullptr);
+// The context's loaded proposal network fits a range of D labels.
+bool proposal_fits(const mpv_ctx *ctx, int D);
+
 // Network input of the top level of `view` (2 + D_top channels, BF16) into out.
 mpv_status enqueue_features(const mpv_params &p, const PairJob &job, uint8_t *workspace,
                             cudaStream_t s, int view, __nv_bfloat16 *out);

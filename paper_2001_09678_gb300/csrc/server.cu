@@ -16,6 +16,7 @@
 #include <deque>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "mpv_internal.cuh"
@@ -71,6 +72,7 @@ struct mpv_server {
     std::deque<mpv_completion> completed;
     uint64_t admitted = 0, evictions = 0;
     int peak_inflight = 0;
+    std::string proposal;            // weights of the learned proposal ("" = pyramid only)
 };
 
 namespace {
@@ -99,7 +101,20 @@ bool make_resident(mpv_server *s, Camera &c, mpv_status &err)
     if ((err = mpv_create(s->device, &ctx)) != MPV_OK) return false;
     mpv_params p = s->params;
     p.max_disparity = c.D;
-    if ((err = mpv_set_params(ctx, &p)) != MPV_OK || (err = mpv_workspace_bytes(ctx, c.W, c.H, &ws)) != MPV_OK) {
+    if ((err = mpv_set_params(ctx, &p)) != MPV_OK) {
+        mpv_destroy(ctx);
+        return false;
+    }
+    if (!s->proposal.empty()) {
+        // the learned proposal where the network fits the camera's range, else the pyramid
+        mpv_params q = p;
+        q.proposal = MPV_PROPOSAL_LEARNED;
+        if (mpv_set_params(ctx, &q) != MPV_OK ||
+            mpv_load_proposal_weights(ctx, s->proposal.c_str()) != MPV_OK ||
+            !mpv::proposal_fits(ctx, c.D))
+            mpv_set_params(ctx, &p);
+    }
+    if ((err = mpv_workspace_bytes(ctx, c.W, c.H, &ws)) != MPV_OK) {
         mpv_destroy(ctx);
         return false;
     }
@@ -210,6 +225,13 @@ mpv_status mpv_server_create(int device, const mpv_params *p, size_t hbm_budget,
     s->budget = hbm_budget;
     s->max_inflight = max_inflight;
     *out = s;
+    return MPV_OK;
+}
+
+mpv_status mpv_server_set_proposal(mpv_server *s, const char *weights_path)
+{
+    if (!s) return MPV_ERR_INVALID_ARG;
+    s->proposal = weights_path ? weights_path : "";
     return MPV_OK;
 }
 

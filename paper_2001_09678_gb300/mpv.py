@@ -83,7 +83,7 @@ class mpv_pair(C.Structure):
 EXPORTS = [
     "mpv_default_params", "mpv_create", "mpv_set_params", "mpv_get_params", "mpv_match",
     "mpv_match_host", "mpv_match_batch", "mpv_load_proposal_weights", "mpv_sync",
-    "mpv_set_gradient_penalty", "mpv_road_detect",
+    "mpv_set_gradient_penalty", "mpv_road_detect", "mpv_server_set_proposal",
     "mpv_workspace_bytes", "mpv_set_workspace_limit", "mpv_debug_stage", "mpv_level_info",
     "mpv_status_string", "mpv_destroy", "mpv_profile_enable", "mpv_profile_read",
     "mpv_match_noalloc", "mpv_autotune", "mpv_server_create", "mpv_server_add_camera",
@@ -131,6 +131,7 @@ def load(path: str = LIB_PATH):
     L.mpv_autotune.argtypes = [ctx, C.POINTER(mpv_pair), C.POINTER(i32)]
     L.mpv_server_create.argtypes = [C.c_int, pp, C.c_size_t, i32, C.POINTER(C.c_void_p)]
     L.mpv_server_add_camera.argtypes = [vp, i32, i32, i32, i32]
+    L.mpv_server_set_proposal.argtypes = [vp, C.c_char_p]
     L.mpv_server_submit.argtypes = [vp, i32, vp, vp, i32, vp, i32, C.c_uint64]
     L.mpv_server_poll.argtypes = [vp, C.POINTER(mpv_completion), i32, C.POINTER(i32)]
     L.mpv_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_size_t),
@@ -348,6 +349,12 @@ def mpv_server_create(params: mpv_params, hbm_budget: int = 0, max_inflight: int
     _check(load().mpv_server_create(device, C.byref(params), hbm_budget, max_inflight,
                                     C.byref(h)), "mpv_server_create")
     return h
+
+
+def mpv_server_set_proposal(server, weights_path) -> None:
+    """Learned proposal for cameras whose range fits the network (None: pyramid only)."""
+    _check(load().mpv_server_set_proposal(server, weights_path.encode() if weights_path else None),
+           "mpv_server_set_proposal")
 
 
 def mpv_server_add_camera(srv, camera: int, width: int, height: int, max_disparity: int):

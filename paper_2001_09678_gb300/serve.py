@@ -74,11 +74,14 @@ def _warm(srv, cams, pools):
 
 
 def run(cams, pools, seconds=5.0, hz=30.0, budget=0, max_inflight=8, params=None,
-        keep_outputs=False, seed=0, warm=True):
-    """Serves every camera's arrivals for `seconds`; returns latencies and stats."""
+        keep_outputs=False, seed=0, warm=True, proposal=None):
+    """Serves every camera's arrivals for `seconds`; returns latencies and stats.
+    proposal: weights of the learned window proposal (cameras whose range fits it)."""
     params = params or mpv.mpv_default_params()
     srv = mpv.mpv_server_create(params, hbm_budget=budget, max_inflight=max_inflight)
     try:
+        if proposal:
+            mpv.mpv_server_set_proposal(srv, proposal)
         events = []
         for cid, W, H, D in cams:
             mpv.mpv_server_add_camera(srv, cid, W, H, D)
@@ -89,7 +92,7 @@ def run(cams, pools, seconds=5.0, hz=30.0, budget=0, max_inflight=8, params=None
         events.sort()
         outputs = {}
         pending = {}
-        lat, status = [], []
+        lat, status, waits, service, sizes, t_arrive = [], [], [], [], [], []
         t0 = time.perf_counter()
         i = 0
         n_done = 0
@@ -108,6 +111,10 @@ def run(cams, pools, seconds=5.0, hz=30.0, budget=0, max_inflight=8, params=None
             for c in mpv.mpv_server_poll(srv):
                 L, R, disp, cid, k = pending.pop(c.request_id)
                 lat.append(c.t_done_ms - c.t_submit_ms)
+                waits.append(c.t_start_ms - c.t_submit_ms)
+                service.append(c.t_done_ms - c.t_start_ms)
+                sizes.append(L.shape[1])
+                t_arrive.append(c.t_submit_ms)
                 status.append(c.status)
                 if keep_outputs:
                     outputs[c.request_id] = (cid, k, disp)
@@ -120,12 +127,27 @@ def run(cams, pools, seconds=5.0, hz=30.0, budget=0, max_inflight=8, params=None
         mpv.mpv_server_destroy(srv)
     lat = np.array(lat)
     ok = np.array(status) == 0
+    waits, service, sizes = np.array(waits), np.array(service), np.array(sizes)
+
+    def pct(a, q):
+        return float(np.percentile(a, q)) if a.size else None
+
+    by_size = {}
+    for w in sorted(set(sizes.tolist())):
+        m = ok & (sizes == w)
+        by_size[f"width{w}"] = dict(frames=int(m.sum()), p50_ms=pct(lat[m], 50),
+                                    p99_ms=pct(lat[m], 99), service_p50_ms=pct(service[m], 50))
     return dict(
         frames=int(len(events)), ok=int(ok.sum()), wall_s=wall,
         fps=float(ok.sum() / wall),
         p50_ms=float(np.percentile(lat[ok], 50)) if ok.any() else None,
         p99_ms=float(np.percentile(lat[ok], 99)) if ok.any() else None,
+        p90_ms=pct(lat[ok], 90), max_ms=float(lat[ok].max()) if ok.any() else None,
+        queue_wait_p50_ms=pct(waits[ok], 50), queue_wait_p99_ms=pct(waits[ok], 99),
+        service_p50_ms=pct(service[ok], 50), service_p99_ms=pct(service[ok], 99),
+        by_size=by_size,
         max_submit_lag_ms=float(1e3 * max(lateness)) if lateness else 0.0,
+        submit_lag_p99_ms=float(1e3 * np.percentile(lateness, 99)) if lateness else 0.0,
         evictions=int(stats["evictions"]), peak_inflight=int(stats["peak_inflight"]),
         outputs=outputs,
     )
@@ -138,6 +160,8 @@ def main():
     ap.add_argument("--budget-mb", type=float, default=0.0)
     ap.add_argument("--max-inflight", type=int, default=8)
     ap.add_argument("--pool", type=int, default=8)
+    ap.add_argument("--learned", default=None,
+                    help="weights of the learned proposal (cameras whose range fits it)")
     args = ap.parse_args()
     mpv.load()
     cams = camera_specs()
@@ -146,10 +170,13 @@ def main():
     import torch
     torch.cuda.init()
     res = run(cams, pools, seconds=args.seconds, hz=args.hz,
-              budget=int(args.budget_mb * 2**20), max_inflight=args.max_inflight)
+              budget=int(args.budget_mb * 2**20), max_inflight=args.max_inflight,
+              proposal=args.learned)
     res.pop("outputs")
+    mode = ("learned proposal where the network fits (1280x720 D128), pyramid elsewhere"
+            if args.learned else "plain 3-scale MPV")
     res["workload"] = "8 cameras (2x640x480 D64, 4x1280x720 D128, 2x1920x1080 D192), " \
-                      f"Poisson {args.hz:g} Hz each, plain 3-scale MPV, 8 paths, LR"
+                      f"Poisson {args.hz:g} Hz each, {mode}, 8 paths, LR"
     print(json.dumps(res))
 
 

@@ -70,3 +70,38 @@ def test_camera_that_cannot_fit_fails_with_oom(setup):
     mpv, pools, alone = setup
     res = serve.run(CAMS[:1], pools, seconds=0.3, hz=30.0, budget=1 << 16, max_inflight=2)
     assert res["ok"] == 0 and res["frames"] > 0
+
+
+def test_learned_proposal_where_the_network_fits(setup):
+    # the committed network takes D = 128 over 3 scales (2 + 32 input channels): the
+    # 256x144 D128 cameras match with the learned proposal, the D32 cameras with the pyramid
+    mpv, _, _ = setup
+    import os
+    weights = os.path.join(os.path.dirname(serve.__file__), "weights", "proposal_d128_s3.bin")
+    cams = [(0, 160, 96, 32), (1, 256, 144, 128), (2, 256, 144, 128)]
+    pools = {(160, 96, 32): [synth.slanted_pair(160, 96, seed=810 + k, d_max=24)[:2]
+                             for k in range(2)],
+             (256, 144, 128): [synth.slanted_pair(256, 144, seed=820 + k, d_max=100)[:2]
+                               for k in range(2)]}
+    alone = {}
+    for (W, H, D), frames in pools.items():
+        ctx = mpv.mpv_create(0)
+        learned = D == 128
+        mpv.mpv_set_params(ctx, mpv.mpv_default_params(
+            max_disparity=D, proposal=mpv.MPV_PROPOSAL_LEARNED if learned else 0))
+        if learned:
+            mpv.mpv_load_proposal_weights(ctx, weights)
+        for k, (L, R) in enumerate(frames):
+            l, r = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+            d = torch.empty((H, W), dtype=torch.int16, device="cuda")
+            mpv.mpv_match(ctx, l, r, d)
+            mpv.mpv_sync(ctx)
+            alone[(W, H, D, k)] = d.cpu().numpy().view(np.uint16)
+        mpv.mpv_destroy(ctx)
+    res = serve.run(cams, pools, seconds=1.0, hz=30.0, max_inflight=4, keep_outputs=True,
+                    proposal=weights)
+    assert res["ok"] == res["frames"] > 50
+    geom = {cid: (W, H, D) for cid, W, H, D in cams}
+    for rid, (cid, k, disp) in res["outputs"].items():
+        W, H, D = geom[cid]
+        assert np.array_equal(disp, alone[(W, H, D, k % 2)]), (rid, cid, k)
