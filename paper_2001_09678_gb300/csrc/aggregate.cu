@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
     constexpr int PAD = (DWP + 4 * HW + 2 + 7) / 8 * 8;  // absent labels around a path
     constexpr int BUF = 2 * PAD + DWP;
     constexpr int PF = KW <= 4 ? 8 : 4;      // prefetch distance (steps)
-    constexpr int CW = KW / 2;               // 32-bit words of cost bytes per lane
+    constexpr int CW = KW >= 2 ? KW / 2 : 1; // 32-bit words of cost bytes per lane
 
     __shared__ __align__(16) uint16_t rbuf[WIN ? kStencilWarps * kPathsPerWarp * BUF : 8];
 
@@ -180,7 +180,9 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
         if (t < n) {
             const int pix = pix0 + t * dpix;
             const uint8_t *src = cbase + (int64_t)pix * DWP;
-            if (CW % 2 == 0) {
+            if (KW == 1) {
+                cq[slot][0] = ld_pin_u16(src);
+            } else if (CW % 2 == 0) {
 #pragma unroll
                 for (int j = 0; j < CW; j += 2) {
                     const uint2 v = ld_pin_u64(src + 4 * j);
@@ -219,10 +221,14 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
             const bool act = t < n;
             const int pix = pix0 + t * dpix;
             uint32_t c[KW];
+            if (KW == 1) {
+                c[0] = __byte_perm(cq[u][0], 0u, 0x4140);
+            } else {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) {
-                c[2 * j] = __byte_perm(cq[u][j], 0u, 0x4140);
-                c[2 * j + 1] = __byte_perm(cq[u][j], 0u, 0x4342);
+                for (int j = 0; j < CW; ++j) {
+                    c[2 * j] = __byte_perm(cq[u][j], 0u, 0x4140);
+                    c[(2 * j + 1) % KW] = __byte_perm(cq[u][j], 0u, 0x4342);
+                }
             }
             const int cur_lo = (int)lq[u];
             issue(t + PF, u);
@@ -341,7 +347,7 @@ void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
         if (win) launch_stencil<G, KW, 2, true, false>(a, s);
         else if (blk) launch_stencil<G, KW, 2, false, true>(a, s);
         else launch_stencil<G, KW, 2, false, false>(a, s);
-    } else {
+    } else if constexpr (KW >= 2) {    // halos of two words need two words per lane
         if (win) launch_stencil<G, KW, 4, true, false>(a, s);
         else if (blk) launch_stencil<G, KW, 4, false, true>(a, s);
         else launch_stencil<G, KW, 4, false, false>(a, s);
@@ -600,7 +606,11 @@ void launch_aggregate(const LevelArgs &a, cudaStream_t s)
     if (a.radius <= 4 && a.Dws <= 64) {
         const bool wide = a.lanes == kLanesWide;
         switch (a.Dws) {
-        case 16: launch_stencil_kw<4, 2>(a, s); return;
+        case 16:
+            // 8 lanes of one word each for the radius-2 stencil, else 4 lanes of two words
+            if (wide && a.radius <= 2) launch_stencil_kw<kLanesWide, 1>(a, s);
+            else launch_stencil_kw<4, 2>(a, s);
+            return;
         case 32:
             if (wide) launch_stencil_kw<kLanesWide, 32 / (2 * kLanesWide)>(a, s);
             else launch_stencil_kw<4, 4>(a, s);

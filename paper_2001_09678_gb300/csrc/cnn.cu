@@ -258,31 +258,50 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// NT: n-tiles of 8 output channels (4: the 32-channel layers; 1: the output layer, its
+// one channel padded to 8 with zero weights)
+template <int NT>
 __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
     const __nv_bfloat16 *__restrict__ in, int Cin, int CP, int H, int W,
-    const __nv_bfloat16 *__restrict__ w, const float *__restrict__ b, int relu,
+    const __nv_bfloat16 *__restrict__ w, const float *__restrict__ b, int Cout, int relu,
     __nv_bfloat16 *__restrict__ out_bf, float *__restrict__ out_f)
 {
+    constexpr int NC = 8 * NT;                           // output channels of the tile
     extern __shared__ __align__(16) __nv_bfloat16 sm[];
     constexpr int TR = kMmaRows + 2, TC = kMmaCols + 2;
     __nv_bfloat16 *xs = sm;                              // [TR][TC][CP]
-    __nv_bfloat16 *ws = sm + TR * TC * CP;               // [32][9][CP]
+    __nv_bfloat16 *ws = sm + TR * TC * CP;               // [NC][9][CP]
     const int n = blockIdx.z;
     const int x0 = blockIdx.x * kMmaCols;
     const int64_t plane = (int64_t)H * W;
     const __nv_bfloat16 *src = in + (int64_t)n * Cin * plane;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
     const int K16 = (Cin + 15) / 16 * 16;                // channels the k-steps cover
-    // weights: one (co, ci) pair per step, its 9 taps contiguous in global memory
-    for (int i = threadIdx.x; i < 32 * Cin; i += 128) {
-        const int co = i / Cin, c = i - co * Cin;
-        const __nv_bfloat16 *wr = w + (int64_t)i * 9;
+    // weights: one (co, ci) pair per step, its 9 taps contiguous in global memory;
+    // output channels Cout .. NC-1 have zero weights
+    for (int i0 = threadIdx.x; i0 < NC * Cin; i0 += 256) {   // two pairs per round
+        __nv_bfloat16 v[2][9];
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) ws[(co * 9 + tap) * CP + c] = wr[tap];
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + h * 128;
+            const int co = i / Cin;
+            const __nv_bfloat16 *wr = w + (int64_t)i * 9;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap)
+                v[h][tap] = (i < NC * Cin && co < Cout) ? wr[tap] : zero;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + h * 128;
+            if (i >= NC * Cin) break;
+            const int co = i / Cin, c = i - co * Cin;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) ws[(co * 9 + tap) * CP + c] = v[h][tap];
+        }
     }
     // channels Cin .. K16-1 are zero in both operands (never rewritten below)
     const int npad = K16 - Cin;
-    for (int i = threadIdx.x; i < 32 * 9 * npad; i += 128)
+    for (int i = threadIdx.x; i < NC * 9 * npad; i += 128)
         ws[(i / npad) * CP + Cin + i % npad] = zero;
     for (int i = threadIdx.x; i < TR * TC * npad; i += 128)
         xs[(i / npad) * CP + Cin + i % npad] = zero;
@@ -296,19 +315,32 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
         const int y0 = (blockIdx.y * kMmaRowTiles + rt) * kMmaRows;
         if (y0 >= H) break;                              // uniform over the block
         __syncthreads();                                 // the previous tile is consumed
-        // input tile, consecutive threads on consecutive pixels of a row
-        for (int i = threadIdx.x; i < TR * TC * Cin; i += 128) {
-            const int px = i % TC, q = i / TC, py = q % TR, c = q / TR;
-            const int yy = y0 - 1 + py, xx = x0 - 1 + px;
-            xs[(py * TC + px) * CP + c] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                                              ? src[c * plane + (int64_t)yy * W + xx] : zero;
+        // input tile, consecutive threads on consecutive pixels of a row; each thread
+        // issues kStageBatch loads before its stores, so that their latencies overlap
+        constexpr int kStageBatch = 8;
+        const int ntile = TR * TC * Cin;
+        for (int i0 = threadIdx.x; i0 < ntile; i0 += 128 * kStageBatch) {
+            __nv_bfloat16 v[kStageBatch];
+            int dst[kStageBatch];
+#pragma unroll
+            for (int b = 0; b < kStageBatch; ++b) {
+                const int i = i0 + b * 128;
+                const int px = i % TC, q = i / TC, py = q % TR, c = q / TR;
+                const int yy = y0 - 1 + py, xx = x0 - 1 + px;
+                const bool in_img = i < ntile && yy >= 0 && yy < H && xx >= 0 && xx < W;
+                v[b] = in_img ? src[c * plane + (int64_t)yy * W + xx] : zero;
+                dst[b] = i < ntile ? (py * TC + px) * CP + c : -1;
+            }
+#pragma unroll
+            for (int b = 0; b < kStageBatch; ++b)
+                if (dst[b] >= 0) xs[dst[b]] = v[b];
         }
         __syncthreads();
-        float acc[2][4][4];
+        float acc[2][NT][4];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
         for (int tap = 0; tap < 9; ++tap) {
@@ -322,7 +354,7 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
                             xs + (py * TC + px) * CP + c0 + acol);
                 }
 #pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
+                for (int nt = 0; nt < NT; ++nt) {
                     unsigned b0, b1;
                     ldsm_x2(b0, b1, ws + ((nt * 8 + brow) * 9 + tap) * CP + c0 + bcol);
 #pragma unroll
@@ -336,15 +368,15 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
         for (int mt = 0; mt < 2; ++mt) {
             const int y = y0 + 2 * warp + mt;
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int x = x0 + g + (e >= 2 ? 8 : 0);
                     const int co = nt * 8 + 2 * t + (e & 1);
-                    if (x >= W || y >= H) continue;
+                    if (x >= W || y >= H || co >= Cout) continue;
                     float v = acc[mt][nt][e] + (b ? b[co] : 0.f);
                     if (relu) v = fmaxf(v, 0.f);
-                    const int64_t o = ((int64_t)n * 32 + co) * plane + (int64_t)y * W + x;
+                    const int64_t o = ((int64_t)n * Cout + co) * plane + (int64_t)y * W + x;
                     if (out_f) out_f[o] = v;
                     if (out_bf) out_bf[o] = __float2bfloat16(v);
                 }
@@ -378,17 +410,27 @@ void launch_conv3x3(const __nv_bfloat16 *in, int N, int Cin, int H, int W, const
                     const float *b, int Cout, int relu, __nv_bfloat16 *out_bf, float *out_f,
                     cudaStream_t s)
 {
-    if (Cout != 32) {
+    if (Cout != 32 && Cout != 1) {
         launch_conv3x3_t(in, N, Cin, H, W, w, b, Cout, relu, out_bf, out_f, s);
         return;
     }
     // channel stride: Cin rounded up to 16 (whole k-steps) plus 8 (bank spread)
     const int CP = (Cin + 15) / 16 * 16 + 8;
-    const size_t smem = sizeof(__nv_bfloat16) * (size_t)CP * ((kMmaRows + 2) * (kMmaCols + 2) + 32 * 9);
+    const int NC = Cout == 32 ? 32 : 8;
+    const size_t smem = sizeof(__nv_bfloat16) * (size_t)CP * ((kMmaRows + 2) * (kMmaCols + 2) + NC * 9);
     const int rows = kMmaRows * kMmaRowTiles;
     dim3 grid((W + kMmaCols - 1) / kMmaCols, (H + rows - 1) / rows, N);
-    cudaFuncSetAttribute(conv3x3_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    conv3x3_mma_kernel<<<grid, 128, smem, s>>>(in, Cin, CP, H, W, w, b, relu, out_bf, out_f);
+    if (Cout == 32) {
+        cudaFuncSetAttribute(conv3x3_mma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        conv3x3_mma_kernel<4><<<grid, 128, smem, s>>>(in, Cin, CP, H, W, w, b, Cout, relu, out_bf,
+                                                      out_f);
+    } else {
+        cudaFuncSetAttribute(conv3x3_mma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        conv3x3_mma_kernel<1><<<grid, 128, smem, s>>>(in, Cin, CP, H, W, w, b, Cout, relu, out_bf,
+                                                      out_f);
+    }
 }
 
 void launch_conv3x3_wgrad(const __nv_bfloat16 *in, int N, int Cin, const float *g, int Cout, int H,

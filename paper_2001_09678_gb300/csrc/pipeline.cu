@@ -365,7 +365,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             }
         }
         {
-            HookScope hs(hook, MPV_STAGE_WTA, 1, s);
+            HookScope hs(hook, MPV_STAGE_WTA, a.edge ? 2 : 1, s);
             launch_wta(a, s);
         }
         if (dbg && l == dbg->level) {

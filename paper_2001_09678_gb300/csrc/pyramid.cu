@@ -132,25 +132,45 @@ __global__ void wta_kernel(LevelArgs a)
     best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 2));
     const int lo = (in && v.lo) ? (int)v.lo[i] : 0;
     if (in && sub == 0) v.d[i] = (uint16_t)(lo + (best & 0xFFFFu));
-    if (a.edge) {   // uniform over the grid: every thread of the block reaches the barriers
-        // the minimum sits on the window's edge while the range continues beyond it
-        __shared__ unsigned counts[2];
-        if (threadIdx.x == 0) counts[0] = counts[1] = 0;
-        __syncthreads();
-        const int k = (int)(best & 0xFFFFu);
-        const bool hit = in && sub == 0 &&
-                         ((k == 0 && lo > 0) || (k == a.Dw - 1 && lo + a.Dw < a.D));
-        const unsigned nh = __popc(__ballot_sync(0xFFFFFFFFu, hit));
-        const unsigned np = __popc(__ballot_sync(0xFFFFFFFFu, in && sub == 0));
-        if ((threadIdx.x & 31) == 0 && np) {
-            atomicAdd(&counts[0], nh);
-            atomicAdd(&counts[1], np);
+}
+
+// Window-edge hits of the learned proposal: pixels whose minimum sits on an edge of
+// their window while the range continues beyond it (k = d - lo is 0 with lo > 0, or
+// Dw - 1 with lo + Dw < D).  A fixed grid strides over the pixels and every block adds
+// its two counts with one pair of atomics.
+constexpr int kEdgeBlocks = 304, kEdgeThreads = 256;
+
+__global__ void __launch_bounds__(kEdgeThreads) edge_kernel(LevelArgs a)
+{
+    const ViewLevel &v = a.v[blockIdx.z];
+    const int64_t npx = (int64_t)a.W * a.H;
+    unsigned hits = 0, px = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kEdgeThreads + threadIdx.x; i < npx;
+         i += (int64_t)kEdgeBlocks * kEdgeThreads) {
+        const int lo = v.lo ? (int)v.lo[i] : 0;
+        const int k = (int)v.d[i] - lo;
+        hits += (k == 0 && lo > 0) || (k == a.Dw - 1 && lo + a.Dw < a.D);
+        ++px;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        hits += __shfl_xor_sync(0xFFFFFFFFu, hits, o);
+        px += __shfl_xor_sync(0xFFFFFFFFu, px, o);
+    }
+    __shared__ unsigned part[2][kEdgeThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+        part[0][threadIdx.x >> 5] = hits;
+        part[1][threadIdx.x >> 5] = px;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long h = 0, p = 0;
+        for (int w = 0; w < kEdgeThreads / 32; ++w) {
+            h += part[0][w];
+            p += part[1][w];
         }
-        __syncthreads();
-        // one pair of global atomics per block instead of per warp
-        if (threadIdx.x == 0 && counts[1]) {
-            atomicAdd(a.edge, (unsigned long long)counts[0]);
-            atomicAdd(a.edge + 1, (unsigned long long)counts[1]);
+        if (p) {
+            atomicAdd(a.edge, h);
+            atomicAdd(a.edge + 1, p);
         }
     }
 }
@@ -221,6 +241,7 @@ void launch_wta(const LevelArgs &a, cudaStream_t s)
     const int64_t nthreads = 4 * (int64_t)a.W * a.H;
     dim3 grid((unsigned)((nthreads + 255) / 256), 1, a.nviews);
     wta_kernel<<<grid, 256, 0, s>>>(a);
+    if (a.edge) edge_kernel<<<dim3(kEdgeBlocks, 1, a.nviews), kEdgeThreads, 0, s>>>(a);
 }
 
 void launch_unpack(const LevelArgs &a, int view, uint16_t *cost, uint32_t *sum, cudaStream_t s)
