@@ -191,6 +191,13 @@ mpv_status mpv_proposal_features(mpv_ctx *ctx, const uint8_t *left, const uint8_
                                  int32_t width, int32_t height, int32_t pitch, int32_t view,
                                  void *out, void *cuda_stream);
 
+/* The learned proposal's raw prediction for one view (proposal = LEARNED, weights
+ * loaded): disparity / D per pixel of the top pyramid level, FP32 [H_top][W_top] into
+ * the device buffer out (sizes from mpv_level_info at level 0).  Asynchronous.         */
+mpv_status mpv_proposal_predict(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                int32_t width, int32_t height, int32_t pitch, int32_t view,
+                                float *out, void *cuda_stream);
+
 /* Of the last mpv_match with the learned proposal (read after mpv_sync): the pixels
  * whose winning label sits on their window's edge while the range continues past it,
  * and the pixels matched (both views).  A high ratio means the windows missed: the

@@ -190,6 +190,32 @@ __global__ void features_kernel(const uint8_t *__restrict__ I0, int p0, const ui
     for (int k = 0; k < Dw; ++k) out[(2 + k) * plane + px] = __float2bfloat16(c[k] * (1.f / 255.f));
 }
 
+// The same features channels-last, cstr channels per pixel (zero beyond 2 + Dw), written
+// in 16-byte pieces: [view][y][x][cstr].
+__global__ void features_nhwc_kernel(const uint8_t *__restrict__ I0, int p0,
+                                     const uint8_t *__restrict__ I1, int p1,
+                                     const uint8_t *__restrict__ C, int Dws, int Dw, int W, int H,
+                                     int cstr, __nv_bfloat16 *__restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W) return;
+    const int64_t px = (int64_t)y * W + x;
+    const uint8_t *c = C + px * Dws;
+    for (int q = 0; q < cstr / 8; ++q) {
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int ch = 8 * q + e;
+            float f = 0.f;
+            if (ch == 0) f = I0[(int64_t)y * p0 + x] * (1.f / 255.f) - 0.5f;
+            else if (ch == 1) f = I1[(int64_t)y * p1 + x] * (1.f / 255.f) - 0.5f;
+            else if (ch - 2 < Dw) f = c[ch - 2] * (1.f / 255.f);
+            v[e] = __float2bfloat16(f);
+        }
+        *(uint4 *)(out + px * cstr + 8 * q) = *(const uint4 *)v;
+    }
+}
+
 // Training target at the top level's resolution: mean of the f x f block of the
 // full-resolution disparity map (blocks clipped at the border), divided by D.
 __global__ void target_kernel(const uint16_t *__restrict__ d, int pitch, int W, int H, int f,
@@ -260,9 +286,12 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
 
 // NT: n-tiles of 8 output channels (4: the 32-channel layers; 1: the output layer, its
 // one channel padded to 8 with zero weights)
-template <int NT>
+// NHWC: activations channels-last, [n][y][x][cstr] with the first Cin channels valid and
+// cstr a multiple of 8 (the pipeline's own buffers: 16-byte copies of whole pixels);
+// otherwise [n][c][y][x] (the public entry points).
+template <int NT, bool NHWC>
 __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
-    const __nv_bfloat16 *__restrict__ in, int Cin, int CP, int H, int W,
+    const __nv_bfloat16 *__restrict__ in, int Cin, int cstr, int CP, int H, int W,
     const __nv_bfloat16 *__restrict__ w, const float *__restrict__ b, int Cout, int relu,
     __nv_bfloat16 *__restrict__ out_bf, float *__restrict__ out_f)
 {
@@ -274,7 +303,7 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
     const int n = blockIdx.z;
     const int x0 = blockIdx.x * kMmaCols;
     const int64_t plane = (int64_t)H * W;
-    const __nv_bfloat16 *src = in + (int64_t)n * Cin * plane;
+    const __nv_bfloat16 *src = in + (int64_t)n * (NHWC ? cstr : Cin) * plane;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
     const int K16 = (Cin + 15) / 16 * 16;                // channels the k-steps cover
     // weights: one (co, ci) pair per step, its 9 taps contiguous in global memory;
@@ -315,6 +344,32 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
         const int y0 = (blockIdx.y * kMmaRowTiles + rt) * kMmaRows;
         if (y0 >= H) break;                              // uniform over the block
         __syncthreads();                                 // the previous tile is consumed
+        if (NHWC) {
+            // whole pixels in 16-byte pieces (cstr / 8 per pixel), consecutive threads on
+            // consecutive pieces, a batch of loads before the stores
+            constexpr int kBatch = 8;
+            const int per = cstr / 8, npieces = TR * TC * per;
+            for (int i0 = threadIdx.x; i0 < npieces; i0 += 128 * kBatch) {
+                uint4 v[kBatch];
+#pragma unroll
+                for (int b2 = 0; b2 < kBatch; ++b2) {
+                    const int i = i0 + b2 * 128;
+                    const int pp = i / per, q = i - pp * per;
+                    const int py = pp / TC, px = pp - py * TC;
+                    const int yy = y0 - 1 + py, xx = x0 - 1 + px;
+                    v[b2] = make_uint4(0u, 0u, 0u, 0u);
+                    if (i < npieces && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                        v[b2] = *(const uint4 *)(src + ((int64_t)yy * W + xx) * cstr + 8 * q);
+                }
+#pragma unroll
+                for (int b2 = 0; b2 < kBatch; ++b2) {
+                    const int i = i0 + b2 * 128;
+                    if (i >= npieces) break;
+                    const int pp = i / per, q = i - pp * per;
+                    *(uint4 *)(xs + pp * CP + 8 * q) = v[b2];
+                }
+            }
+        } else {
         // input tile, consecutive threads on consecutive pixels of a row; each thread
         // issues kStageBatch loads before its stores, so that their latencies overlap
         constexpr int kStageBatch = 8;
@@ -334,6 +389,7 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
 #pragma unroll
             for (int b = 0; b < kStageBatch; ++b)
                 if (dst[b] >= 0) xs[dst[b]] = v[b];
+        }
         }
         __syncthreads();
         float acc[2][NT][4];
@@ -376,7 +432,8 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
                     if (x >= W || y >= H || co >= Cout) continue;
                     float v = acc[mt][nt][e] + (b ? b[co] : 0.f);
                     if (relu) v = fmaxf(v, 0.f);
-                    const int64_t o = ((int64_t)n * Cout + co) * plane + (int64_t)y * W + x;
+                    const int64_t o = NHWC ? ((int64_t)n * plane + (int64_t)y * W + x) * Cout + co
+                                           : ((int64_t)n * Cout + co) * plane + (int64_t)y * W + x;
                     if (out_f) out_f[o] = v;
                     if (out_bf) out_bf[o] = __float2bfloat16(v);
                 }
@@ -406,6 +463,38 @@ void launch_conv3x3_t(const TIn *in, int N, int Cin, int H, int W, const __nv_bf
     }
 }
 
+template <bool NHWC>
+void launch_mma(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
+                const __nv_bfloat16 *w, const float *b, int Cout, int relu, __nv_bfloat16 *out_bf,
+                float *out_f, cudaStream_t s)
+{
+    // channel stride: Cin rounded up to 16 (whole k-steps) plus 8 (bank spread)
+    const int CP = (Cin + 15) / 16 * 16 + 8;
+    const int NC = Cout == 32 ? 32 : 8;
+    const size_t smem =
+        sizeof(__nv_bfloat16) * (size_t)CP * ((kMmaRows + 2) * (kMmaCols + 2) + NC * 9);
+    const int rows = kMmaRows * kMmaRowTiles;
+    dim3 grid((W + kMmaCols - 1) / kMmaCols, (H + rows - 1) / rows, N);
+    if (Cout == 32) {
+        cudaFuncSetAttribute(conv3x3_mma_kernel<4, NHWC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        conv3x3_mma_kernel<4, NHWC><<<grid, 128, smem, s>>>(in, Cin, cstr, CP, H, W, w, b, Cout,
+                                                            relu, out_bf, out_f);
+    } else {
+        cudaFuncSetAttribute(conv3x3_mma_kernel<1, NHWC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        conv3x3_mma_kernel<1, NHWC><<<grid, 128, smem, s>>>(in, Cin, cstr, CP, H, W, w, b, Cout,
+                                                            relu, out_bf, out_f);
+    }
+}
+
+void launch_conv3x3_nhwc(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
+                         const __nv_bfloat16 *w, const float *b, int Cout, int relu,
+                         __nv_bfloat16 *out_bf, float *out_f, cudaStream_t s)
+{
+    launch_mma<true>(in, N, Cin, cstr, H, W, w, b, Cout, relu, out_bf, out_f, s);
+}
+
 void launch_conv3x3(const __nv_bfloat16 *in, int N, int Cin, int H, int W, const __nv_bfloat16 *w,
                     const float *b, int Cout, int relu, __nv_bfloat16 *out_bf, float *out_f,
                     cudaStream_t s)
@@ -414,23 +503,7 @@ void launch_conv3x3(const __nv_bfloat16 *in, int N, int Cin, int H, int W, const
         launch_conv3x3_t(in, N, Cin, H, W, w, b, Cout, relu, out_bf, out_f, s);
         return;
     }
-    // channel stride: Cin rounded up to 16 (whole k-steps) plus 8 (bank spread)
-    const int CP = (Cin + 15) / 16 * 16 + 8;
-    const int NC = Cout == 32 ? 32 : 8;
-    const size_t smem = sizeof(__nv_bfloat16) * (size_t)CP * ((kMmaRows + 2) * (kMmaCols + 2) + NC * 9);
-    const int rows = kMmaRows * kMmaRowTiles;
-    dim3 grid((W + kMmaCols - 1) / kMmaCols, (H + rows - 1) / rows, N);
-    if (Cout == 32) {
-        cudaFuncSetAttribute(conv3x3_mma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        conv3x3_mma_kernel<4><<<grid, 128, smem, s>>>(in, Cin, CP, H, W, w, b, Cout, relu, out_bf,
-                                                      out_f);
-    } else {
-        cudaFuncSetAttribute(conv3x3_mma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        conv3x3_mma_kernel<1><<<grid, 128, smem, s>>>(in, Cin, CP, H, W, w, b, Cout, relu, out_bf,
-                                                      out_f);
-    }
+    launch_mma<false>(in, N, Cin, Cin, H, W, w, b, Cout, relu, out_bf, out_f, s);
 }
 
 void launch_conv3x3_wgrad(const __nv_bfloat16 *in, int N, int Cin, const float *g, int Cout, int H,
@@ -446,6 +519,14 @@ void launch_features(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const
                      int Dws, int Dw, int W, int H, __nv_bfloat16 *out, cudaStream_t s)
 {
     features_kernel<<<dim3(blocks(W, 128), H), 128, 0, s>>>(I0, p0, I1, p1, C, Dws, Dw, W, H, out);
+}
+
+void launch_features_nhwc(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const uint8_t *C,
+                          int Dws, int Dw, int W, int H, int cstr, __nv_bfloat16 *out,
+                          cudaStream_t s)
+{
+    features_nhwc_kernel<<<dim3(blocks(W, 128), H), 128, 0, s>>>(I0, p0, I1, p1, C, Dws, Dw, W,
+                                                                 H, cstr, out);
 }
 
 void launch_proposal_windows(const float *q, int Wq, int Hq, int f, int W, int H, int D, int Dw,

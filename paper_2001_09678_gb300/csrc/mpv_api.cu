@@ -821,6 +821,25 @@ mpv_status mpv_set_workspace_limit(mpv_ctx *ctx, size_t bytes)
     return MPV_OK;
 }
 
+mpv_status mpv_proposal_predict(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                int32_t width, int32_t height, int32_t pitch, int32_t view,
+                                float *out, void *cuda_stream)
+{
+    if (!ctx || !left || !right || !out || view < 0 || view > 1) return MPV_ERR_INVALID_ARG;
+    if (ctx->p.proposal != MPV_PROPOSAL_LEARNED) return MPV_ERR_INVALID_ARG;
+    const mpv_status st =
+        validate_pair(ctx->p, width, height, pitch, width, ctx->p.max_disparity);
+    if (st != MPV_OK) return st;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    StageSink dbg;
+    dbg.view = view;
+    dbg.level = 0;
+    dbg.proposal = out;
+    PairJob j{left, right, width, height, pitch, ctx->p.max_disparity, nullptr, width, nullptr};
+    return enqueue(ctx, j, s, &dbg);
+}
+
 mpv_status mpv_debug_stage(mpv_ctx *ctx, const uint8_t *left, const uint8_t *right,
                            int32_t width, int32_t height, int32_t pitch, int32_t view,
                            int32_t level, uint16_t *lo, uint16_t *cost, uint32_t *sum,

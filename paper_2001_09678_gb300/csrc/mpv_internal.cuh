@@ -126,6 +126,15 @@ void launch_conv3x3(const __nv_bfloat16 *in, int N, int Cin, int H, int W, const
                     cudaStream_t s);
 void launch_features(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const uint8_t *C,
                      int Dws, int Dw, int W, int H, __nv_bfloat16 *out, cudaStream_t s);
+// channels-last forms used by the matcher's own proposal network (cstr: multiple of 8)
+void launch_features_nhwc(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const uint8_t *C,
+                          int Dws, int Dw, int W, int H, int cstr, __nv_bfloat16 *out,
+                          cudaStream_t s);
+void launch_conv3x3_nhwc(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
+                         const __nv_bfloat16 *w, const float *b, int Cout, int relu,
+                         __nv_bfloat16 *out_bf, float *out_f, cudaStream_t s);
+// channels per pixel of the network input in the matcher's buffers
+inline int feature_stride(int Dw_top) { return (2 + Dw_top + 7) / 8 * 8; }
 void launch_proposal_windows(const float *q, int Wq, int Hq, int f, int W, int H, int D, int Dw,
                              uint16_t *lo, cudaStream_t s);
 
@@ -167,6 +176,7 @@ struct StageSink {
     int view = -1, level = -1;
     uint16_t *lo = nullptr, *cost = nullptr, *disp = nullptr;
     uint32_t *sum = nullptr;
+    float *proposal = nullptr;   // learned proposal: the network's top-level prediction
 };
 
 bool params_valid(const mpv_params &p);

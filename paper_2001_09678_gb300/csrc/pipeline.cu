@@ -136,7 +136,7 @@ Layout make_layout(const Geometry &g, int nviews, const mpv_params &p)
     }
     if (learned) {
         const size_t px0 = (size_t)g.W[0] * g.H[0];
-        L.feat = take(off, 2 * sizeof(__nv_bfloat16) * (size_t)(2 + g.Dw[0]) * px0);
+        L.feat = take(off, 2 * sizeof(__nv_bfloat16) * (size_t)feature_stride(g.Dw[0]) * px0);
         L.act0 = take(off, 2 * sizeof(__nv_bfloat16) * 32 * px0);
         L.act1 = take(off, 2 * sizeof(__nv_bfloat16) * 32 * px0);
         L.q = take(off, 2 * sizeof(float) * px0);
@@ -295,23 +295,31 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
         }
         if (learned && l == 0) {
             HookScope hs(hook, MPV_STAGE_SEED, 2 + net->layers, s);
+            // channels-last activations: the network input padded to a multiple of 8
+            // channels, the hidden layers 32 channels per pixel
             const size_t px0 = (size_t)a.W * a.H;
-            const int cin0 = 2 + a.Dw;
+            const int cstr0 = feature_stride(a.Dw);
             __nv_bfloat16 *feat = (__nv_bfloat16 *)(base + L.feat);
             for (int v = 0; v < nviews; ++v)
-                launch_features(a.v[v].I0, a.v[v].pitch0, a.v[v].I1, a.v[v].pitch1, a.v[v].C,
-                                a.Dws, a.Dw, a.W, a.H, feat + v * cin0 * px0, s);
+                launch_features_nhwc(a.v[v].I0, a.v[v].pitch0, a.v[v].I1, a.v[v].pitch1,
+                                     a.v[v].C, a.Dws, a.Dw, a.W, a.H, cstr0,
+                                     feat + v * cstr0 * px0, s);
             const __nv_bfloat16 *in = feat;
+            int cstr = cstr0;
             __nv_bfloat16 *bufs[2] = {(__nv_bfloat16 *)(base + L.act0),
                                       (__nv_bfloat16 *)(base + L.act1)};
             for (int k = 0; k < net->layers; ++k) {
                 const bool lastk = k + 1 == net->layers;
-                launch_conv3x3(in, nviews, net->cin[k], a.H, a.W,
-                               (const __nv_bfloat16 *)net->w[k], net->b[k], net->cout[k],
-                               net->relu[k], lastk ? nullptr : bufs[k & 1],
-                               lastk ? (float *)(base + L.q) : nullptr, s);
+                launch_conv3x3_nhwc(in, nviews, net->cin[k], cstr, a.H, a.W,
+                                    (const __nv_bfloat16 *)net->w[k], net->b[k], net->cout[k],
+                                    net->relu[k], lastk ? nullptr : bufs[k & 1],
+                                    lastk ? (float *)(base + L.q) : nullptr, s);
                 in = bufs[k & 1];
+                cstr = net->cout[k];
             }
+            if (dbg && dbg->proposal)
+                cudaMemcpyAsync(dbg->proposal, (const float *)(base + L.q) + dbg->view * px0,
+                                px0 * sizeof(float), cudaMemcpyDeviceToDevice, s);
             if (!(dbg && dbg->level == 0)) continue;
         }
         if (layered) {

@@ -90,7 +90,7 @@ EXPORTS = [
     "mpv_server_submit", "mpv_server_poll", "mpv_server_stats", "mpv_server_destroy",
     "mpv_cnn_conv3x3", "mpv_cnn_conv3x3_wgrad", "mpv_cnn_flip_transpose",
     "mpv_cnn_relu_backward", "mpv_cnn_huber", "mpv_cnn_adam", "mpv_cnn_to_bf16",
-    "mpv_cnn_target", "mpv_proposal_features", "mpv_proposal_stats",
+    "mpv_cnn_target", "mpv_proposal_features", "mpv_proposal_stats", "mpv_proposal_predict",
 ]
 MPV_NOALLOC_SCRATCH_BYTES = 64 << 20
 MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
@@ -148,6 +148,7 @@ def load(path: str = LIB_PATH):
                                i32, vp, vp]
     L.mpv_cnn_to_bf16.argtypes = [vp, vp, i64, vp]
     L.mpv_cnn_target.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp]
+    L.mpv_proposal_predict.argtypes = [ctx, vp, vp, i32, i32, i32, i32, vp, vp]
     L.mpv_proposal_features.argtypes = [ctx, vp, vp, i32, i32, i32, i32, vp, vp]
     L.mpv_proposal_stats.argtypes = [ctx, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     L.mpv_destroy.argtypes = [ctx]
@@ -439,6 +440,13 @@ def mpv_cnn_target(disp, factor, max_disparity, target, stream=None):
     H, W = disp.shape[-2], disp.shape[-1]
     _check(load().mpv_cnn_target(_ptr(disp), disp.stride(-2), W, H, factor, max_disparity,
                                  _ptr(target), _stream(stream)), "mpv_cnn_target")
+
+
+def mpv_proposal_predict(ctx, left, right, view, out, stream=None) -> None:
+    """The learned proposal's top-level prediction (disparity / D) of one view, FP32."""
+    H, W = left.shape[-2], left.shape[-1]
+    _check(load().mpv_proposal_predict(ctx, _ptr(left), _ptr(right), W, H, left.stride(-2), view,
+                                       _ptr(out), _stream(stream)), "mpv_proposal_predict")
 
 
 def mpv_proposal_features(ctx, left, right, view, out, stream=None):

@@ -111,3 +111,32 @@ def test_learned_requires_weights_and_matching_channels(m):
             m.mpv_load_proposal_weights(ctx, "/nonexistent/weights.bin")
     finally:
         m.mpv_destroy(ctx)
+
+
+def test_pipeline_prediction_equals_the_network_kernels(m):
+    # the matcher runs the network channels-last; the training kernels run it planar: the
+    # same BF16 operands and the same FP32 accumulation order give the same prediction
+    from paper_2001_09678_gb300 import learn
+    L, R, _ = synth.slanted_pair(200, 120, seed=34, d_max=56)
+    path, layers = _weights_file(2 + 16, seed=5)
+    ctx = m.mpv_create(0)
+    pyr = m.mpv_create(0)
+    try:
+        m.mpv_set_params(ctx, m.mpv_default_params(proposal=m.MPV_PROPOSAL_LEARNED, **KW))
+        m.mpv_load_proposal_weights(ctx, path)
+        m.mpv_set_params(pyr, m.mpv_default_params(**KW))
+        l, r = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+        Wq, Hq = m.mpv_level_info(ctx, 200, 120, 0)[:2]
+        net = learn.Net(layers)
+        for view in (0, 1):
+            q = torch.full((Hq, Wq), -1.0, device="cuda")
+            m.mpv_proposal_predict(ctx, l, r, view, q)
+            feat = torch.empty((18, Hq, Wq), dtype=torch.bfloat16, device="cuda")
+            m.mpv_proposal_features(pyr, l, r, view, feat)
+            torch.cuda.synchronize()
+            pred, _ = net.forward(feat[None])
+            assert torch.equal(q, pred[0, 0]), float((q - pred[0, 0]).abs().max())
+    finally:
+        m.mpv_destroy(ctx)
+        m.mpv_destroy(pyr)
+        os.unlink(path)
