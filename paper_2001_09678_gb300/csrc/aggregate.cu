@@ -590,8 +590,254 @@ void launch_general_k(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------
+// agg_scan8: the general passes with 8 lanes per scan path (4 paths per warp), K labels
+// per lane as 32-bit integers, for strides of 8K labels.  Same arithmetic as agg_general
+// (prefix minima of A(j) - pu j and suffix minima of A(j) + pd j, and of A itself for the
+// asymmetric caps), with the scans over the path's 8 lanes (3 shuffle rounds) instead of
+// a whole warp (5 rounds); re-indexing through shared memory when a window moved.
+// ---------------------------------------------------------------------------------
+constexpr int kScan8Warps = 4;
+
+template <int K, bool WIN>
+__global__ void __launch_bounds__(kScan8Warps * 32) agg_scan8(LevelArgs a, MergeArgs m)
+{
+    constexpr int G = 8, PPW = 32 / G, DWP = G * K, NJ = DWP;
+    const int view = blockIdx.z;
+    const int dir = m.dir0 + blockIdx.y;
+    const int dx = c_dirs[dir][0], dy = c_dirs[dir][1];
+    const int W = a.W, H = a.H, Dw = a.Dw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane & (G - 1), grp = lane / G;
+    const int path = (blockIdx.x * kScan8Warps + warp) * PPW + grp;
+    const ViewLevel &V = a.v[view];
+    const int T = a.trunc;
+    const bool dbl = dir == m.double_up_dir;
+    const int Tu = dbl ? 2 * T : T;
+    const uint16_t *qa = view ? m.qa[1] : m.qa[0];
+    const uint16_t *qb = view ? m.qb[1] : m.qb[0];
+    uint16_t *const *outs = view ? m.out[1] : m.out[0];
+    uint16_t *out = (dir & 1) ? outs[1] : outs[0];
+
+    // per path: prefix/suffix minima for re-indexing, [4][NJ + 1]
+    __shared__ int rbuf[WIN ? kScan8Warps * PPW * 4 * (NJ + 1) : 4];
+    int *pB = rbuf + (WIN ? (warp * PPW + grp) * 4 * (NJ + 1) : 0);
+    int *sC = pB + (NJ + 1), *pA = sC + (NJ + 1), *sA = pA + (NJ + 1);
+
+    int x0 = 0, y0 = 0, n = 0;
+    if (path < num_paths_dir(dx, dy, W, H)) {
+        path_start(dx, dy, W, H, path, x0, y0);
+        n = path_length(dx, dy, W, H, x0, y0);
+    }
+    const int nmax = __reduce_max_sync(kFull, n);
+    int A[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) A[t] = kInf;
+    int prev_lo = 0, prev_i = 0;
+    int x = x0, y = y0;
+    for (int step = 0; step < nmax; ++step, x += dx, y += dy) {
+        const bool act = step < n;
+        const int64_t pix = act ? (int64_t)y * W + x : 0;
+        const int cur_lo = (act && V.lo) ? (int)V.lo[pix] : 0;
+        // data term of this lane's K labels
+        int c[K];
+        if (m.in_mode == 0) {
+            const uint8_t *cp = V.C + pix * DWP + gl * K;
+            if (K % 4 == 0) {   // 4-byte words at 4-byte aligned offsets
+#pragma unroll
+                for (int t = 0; t < K; t += 4) {
+                    const uint32_t wd = act ? *(const uint32_t *)(cp + t) : 0u;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) c[(t + e) % K] = (wd >> (8 * e)) & 0xFF;
+                }
+            } else {            // K = 2: one 2-byte word at an even offset
+                const uint32_t wd = act ? *(const uint16_t *)cp : 0u;
+                c[0] = wd & 0xFF;
+                c[1 % K] = (wd >> 8) & 0xFF;
+            }
+        } else {
+            const uint16_t *pa_ = qa + pix * DWP + gl * K, *pb_ = qb + pix * DWP + gl * K;
+#pragma unroll
+            for (int t = 0; t < K; t += 2) {
+                const uint32_t wa = act ? *(const uint32_t *)(pa_ + t) : 0u;
+                const uint32_t wb = act ? *(const uint32_t *)(pb_ + t) : 0u;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ea = (wa >> (16 * e)) & 0xFFFF, eb = (wb >> (16 * e)) & 0xFFFF;
+                    c[t + e] = m.in_mode == 1 ? min(ea, eb) : (ea + eb) >> 1;
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < K; ++t)
+            if (gl * K + t >= Dw) c[t] = 0;
+        const int cur_i = (m.lut && act) ? (int)V.I0[(int64_t)y * V.pitch0 + x] : 0;
+        bool first = step == 0;
+        if (a.block_cut > 0 && !first &&
+            (x / a.block_cut != (x - dx) / a.block_cut || y / a.block_cut != (y - dy) / a.block_cut))
+            first = true;
+        int L[K];
+        if (__all_sync(kFull, first || !act)) {   // every path of the warp starts here
+#pragma unroll
+            for (int t = 0; t < K; ++t) L[t] = c[t];
+        } else {
+            // a path starting here (first pixel or tile edge) behaves as a predecessor of
+            // infinite energy everywhere: L = c
+            if (first) {
+#pragma unroll
+                for (int t = 0; t < K; ++t) A[t] = kInf;
+            }
+            const int P = m.lut ? min(m.lut[abs(cur_i - prev_i)], T) : a.p1;
+            const int pu = dbl ? 2 * P : P, pd = P;
+            int mn = A[0];
+#pragma unroll
+            for (int t = 1; t < K; ++t) mn = min(mn, A[t]);
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+            const int amin = mn;
+            int pb[K], sc[K], pa[K], sa[K];
+            int run = kInf, runa = kInf;
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                run = min(run, A[t] - pu * (gl * K + t));
+                runa = min(runa, A[t]);
+                pb[t] = run;
+                pa[t] = runa;
+            }
+            int incl = run, incla = runa;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o, G);
+                const int va = __shfl_up_sync(kFull, incla, o, G);
+                if (gl >= o) {
+                    incl = min(incl, v);
+                    incla = min(incla, va);
+                }
+            }
+            int excl = __shfl_up_sync(kFull, incl, 1, G);
+            int excla = __shfl_up_sync(kFull, incla, 1, G);
+            if (gl == 0) excl = excla = kInf;
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                pb[t] = min(pb[t], excl);
+                pa[t] = min(pa[t], excla);
+            }
+            run = runa = kInf;
+#pragma unroll
+            for (int t = K - 1; t >= 0; --t) {
+                run = min(run, A[t] + pd * (gl * K + t));
+                runa = min(runa, A[t]);
+                sc[t] = run;
+                sa[t] = runa;
+            }
+            incl = run;
+            incla = runa;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const int v = __shfl_down_sync(kFull, incl, o, G);
+                const int va = __shfl_down_sync(kFull, incla, o, G);
+                if (gl + o < G) {
+                    incl = min(incl, v);
+                    incla = min(incla, va);
+                }
+            }
+            excl = __shfl_down_sync(kFull, incl, 1, G);
+            excla = __shfl_down_sync(kFull, incla, 1, G);
+            if (gl == G - 1) excl = excla = kInf;
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                sc[t] = min(sc[t], excl);
+                sa[t] = min(sa[t], excla);
+            }
+            const int s = (WIN && act && !first) ? cur_lo - prev_lo : 0;
+            if (WIN && __any_sync(kFull, s != 0)) {
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    pB[gl * K + t + 1] = pb[t];
+                    sC[gl * K + t] = sc[t];
+                    pA[gl * K + t + 1] = pa[t];
+                    sA[gl * K + t] = sa[t];
+                }
+                if (gl == 0) {
+                    pB[0] = pA[0] = kInf;
+                    sC[NJ] = sA[NJ] = kInf;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    const int jj = s + gl * K + t;   // label index in the predecessor window
+                    const int pi = min(max(jj, -1), NJ - 1) + 1;
+                    const int si = min(max(jj, 0), NJ);
+                    int M = min(pu * jj + pB[pi], sC[si] - pd * jj);
+                    M = dbl ? min(M, min(pA[pi] + Tu, sA[si] + T)) : min(M, amin + T);
+                    L[t] = c[t] + M - amin;
+                }
+                __syncwarp();
+            } else {
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    const int j = gl * K + t;
+                    int M = min(pu * j + pb[t], sc[t] - pd * j);
+                    M = dbl ? min(M, min(pa[t] + Tu, sa[t] + T)) : min(M, amin + T);
+                    L[t] = c[t] + M - amin;
+                }
+            }
+            if (first) {
+#pragma unroll
+                for (int t = 0; t < K; ++t) L[t] = c[t];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < K; ++t)
+            if (gl * K + t >= Dw) L[t] = 0;
+        if (m.out_mode == 0) {
+            uint16_t *sp = V.S + pix * DWP + gl * K;
+#pragma unroll
+            for (int t = 0; t < K; t += 2)
+                if (act) atomicAdd((unsigned int *)(sp + t), (unsigned)L[t] | ((unsigned)L[t + 1] << 16));
+        } else {
+            int lm = kInf;
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+                if (gl * K + t < Dw) lm = min(lm, L[t]);
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) lm = min(lm, __shfl_xor_sync(kFull, lm, o));
+            uint16_t *op = out + pix * DWP + gl * K;
+#pragma unroll
+            for (int t = 0; t < K; t += 2) {
+                const unsigned lo16 = gl * K + t < Dw ? (unsigned)(L[t] - lm) : 0u;
+                const unsigned hi16 = gl * K + t + 1 < Dw ? (unsigned)(L[t + 1] - lm) : 0u;
+                if (act) *(unsigned int *)(op + t) = lo16 | (hi16 << 16);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < K; ++t) A[t] = gl * K + t < Dw ? L[t] : kInf;
+        prev_lo = cur_lo;
+        prev_i = cur_i;
+    }
+}
+
+template <int K>
+void launch_scan8_k(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
+{
+    const int maxp = a.W + a.H - 1;
+    const int per_block = kScan8Warps * (32 / 8);
+    dim3 grid((maxp + per_block - 1) / per_block, m.ndirs, a.nviews);
+    if (a.v[0].lo)
+        agg_scan8<K, true><<<grid, kScan8Warps * 32, 0, s>>>(a, m);
+    else
+        agg_scan8<K, false><<<grid, kScan8Warps * 32, 0, s>>>(a, m);
+}
+
 void launch_aggregate_general(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
 {
+    // 8 lanes per path for the strides of 16, 32 and 64 labels
+    switch (a.Dws) {
+    case 16: launch_scan8_k<2>(a, m, s); return;
+    case 32: launch_scan8_k<4>(a, m, s); return;
+    case 64: launch_scan8_k<8>(a, m, s); return;
+    default: break;
+    }
     const int K = (a.Dw + 31) / 32;
     if (K <= 1) launch_general_k<1>(a, m, s);
     else if (K <= 2) launch_general_k<2>(a, m, s);
