@@ -88,6 +88,12 @@ __device__ __forceinline__ uint2 ld_pin_u64(const void *p)
     asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
     return v;
 }
+__device__ __forceinline__ uint32_t ld_pin_u8(const void *p)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.u8 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
 __device__ __forceinline__ uint32_t ld_pin_u16(const void *p)
 {
     unsigned short v;
@@ -603,6 +609,8 @@ template <int K, bool WIN>
 __global__ void __launch_bounds__(kScan8Warps * 32) agg_scan8(LevelArgs a, MergeArgs m)
 {
     constexpr int G = 8, PPW = 32 / G, DWP = G * K, NJ = DWP;
+    constexpr int PF = 4;                    // prefetch distance (steps)
+    constexpr int QW = K / 2;                // 32-bit words of one u16 volume per lane
     const int view = blockIdx.z;
     const int dir = m.dir0 + blockIdx.y;
     const int dx = c_dirs[dir][0], dy = c_dirs[dir][1];
@@ -630,190 +638,215 @@ __global__ void __launch_bounds__(kScan8Warps * 32) agg_scan8(LevelArgs a, Merge
         n = path_length(dx, dy, W, H, x0, y0);
     }
     const int nmax = __reduce_max_sync(kFull, n);
+    const int64_t pix0 = (int64_t)y0 * W + x0, dpix = (int64_t)dy * W + dx;
+    const int64_t ipix0 = (int64_t)y0 * V.pitch0 + x0, dipix = (int64_t)dy * V.pitch0 + dx;
+
+    // prefetch ring: the data term words, the window start and the intensity of the next
+    // PF pixels, loaded PF steps ahead with pinned loads
+    uint32_t qr[PF][2 * QW > 1 ? 2 * QW : 1];
+    uint32_t lr[PF], ir[PF];
+    auto issue = [&](int t, int slot) {
+        if (t < n) {
+            const int64_t pix = pix0 + t * dpix;
+            if (m.in_mode == 0) {
+                const uint8_t *cp = V.C + pix * DWP + gl * K;
+                if (K % 4 == 0) {
+#pragma unroll
+                    for (int j = 0; j < K / 4; ++j) qr[slot][j] = ld_pin_u32(cp + 4 * j);
+                } else {
+                    qr[slot][0] = ld_pin_u16(cp);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < QW; ++j) {
+                    qr[slot][j] = ld_pin_u32(qa + pix * DWP + gl * K + 2 * j);
+                    qr[slot][QW + j] = ld_pin_u32(qb + pix * DWP + gl * K + 2 * j);
+                }
+            }
+            lr[slot] = V.lo ? ld_pin_u16(V.lo + pix) : 0u;
+            ir[slot] = m.lut ? ld_pin_u8(V.I0 + ipix0 + t * dipix) : 0u;
+        }
+    };
+#pragma unroll
+    for (int u = 0; u < PF; ++u) issue(u, u);
+
     int A[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) A[t] = kInf;
     int prev_lo = 0, prev_i = 0;
-    int x = x0, y = y0;
-    for (int step = 0; step < nmax; ++step, x += dx, y += dy) {
-        const bool act = step < n;
-        const int64_t pix = act ? (int64_t)y * W + x : 0;
-        const int cur_lo = (act && V.lo) ? (int)V.lo[pix] : 0;
-        // data term of this lane's K labels
-        int c[K];
-        if (m.in_mode == 0) {
-            const uint8_t *cp = V.C + pix * DWP + gl * K;
-            if (K % 4 == 0) {   // 4-byte words at 4-byte aligned offsets
+    for (int t0 = 0; t0 < nmax; t0 += PF) {
 #pragma unroll
-                for (int t = 0; t < K; t += 4) {
-                    const uint32_t wd = act ? *(const uint32_t *)(cp + t) : 0u;
+        for (int u = 0; u < PF; ++u) {
+            const int step = t0 + u;
+            if (step >= nmax) break;
+            const bool act = step < n;
+            const int x = x0 + step * dx, y = y0 + step * dy;
+            const int64_t pix = act ? pix0 + step * dpix : 0;
+            const int cur_lo = (int)lr[u];
+            const int cur_i = (int)ir[u];
+            // data term of this lane's K labels
+            int c[K];
+            if (m.in_mode == 0) {
+                if (K % 4 == 0) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) c[(t + e) % K] = (wd >> (8 * e)) & 0xFF;
+                    for (int t = 0; t < K; ++t) c[t] = (qr[u][t / 4] >> (8 * (t % 4))) & 0xFF;
+                } else {
+                    c[0] = qr[u][0] & 0xFF;
+                    c[1 % K] = (qr[u][0] >> 8) & 0xFF;
                 }
-            } else {            // K = 2: one 2-byte word at an even offset
-                const uint32_t wd = act ? *(const uint16_t *)cp : 0u;
-                c[0] = wd & 0xFF;
-                c[1 % K] = (wd >> 8) & 0xFF;
-            }
-        } else {
-            const uint16_t *pa_ = qa + pix * DWP + gl * K, *pb_ = qb + pix * DWP + gl * K;
-#pragma unroll
-            for (int t = 0; t < K; t += 2) {
-                const uint32_t wa = act ? *(const uint32_t *)(pa_ + t) : 0u;
-                const uint32_t wb = act ? *(const uint32_t *)(pb_ + t) : 0u;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int ea = (wa >> (16 * e)) & 0xFFFF, eb = (wb >> (16 * e)) & 0xFFFF;
-                    c[t + e] = m.in_mode == 1 ? min(ea, eb) : (ea + eb) >> 1;
-                }
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < K; ++t)
-            if (gl * K + t >= Dw) c[t] = 0;
-        const int cur_i = (m.lut && act) ? (int)V.I0[(int64_t)y * V.pitch0 + x] : 0;
-        bool first = step == 0;
-        if (a.block_cut > 0 && !first &&
-            (x / a.block_cut != (x - dx) / a.block_cut || y / a.block_cut != (y - dy) / a.block_cut))
-            first = true;
-        int L[K];
-        if (__all_sync(kFull, first || !act)) {   // every path of the warp starts here
-#pragma unroll
-            for (int t = 0; t < K; ++t) L[t] = c[t];
-        } else {
-            // a path starting here (first pixel or tile edge) behaves as a predecessor of
-            // infinite energy everywhere: L = c
-            if (first) {
-#pragma unroll
-                for (int t = 0; t < K; ++t) A[t] = kInf;
-            }
-            const int P = m.lut ? min(m.lut[abs(cur_i - prev_i)], T) : a.p1;
-            const int pu = dbl ? 2 * P : P, pd = P;
-            int mn = A[0];
-#pragma unroll
-            for (int t = 1; t < K; ++t) mn = min(mn, A[t]);
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
-            const int amin = mn;
-            int pb[K], sc[K], pa[K], sa[K];
-            int run = kInf, runa = kInf;
-#pragma unroll
-            for (int t = 0; t < K; ++t) {
-                run = min(run, A[t] - pu * (gl * K + t));
-                runa = min(runa, A[t]);
-                pb[t] = run;
-                pa[t] = runa;
-            }
-            int incl = run, incla = runa;
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) {
-                const int v = __shfl_up_sync(kFull, incl, o, G);
-                const int va = __shfl_up_sync(kFull, incla, o, G);
-                if (gl >= o) {
-                    incl = min(incl, v);
-                    incla = min(incla, va);
-                }
-            }
-            int excl = __shfl_up_sync(kFull, incl, 1, G);
-            int excla = __shfl_up_sync(kFull, incla, 1, G);
-            if (gl == 0) excl = excla = kInf;
-#pragma unroll
-            for (int t = 0; t < K; ++t) {
-                pb[t] = min(pb[t], excl);
-                pa[t] = min(pa[t], excla);
-            }
-            run = runa = kInf;
-#pragma unroll
-            for (int t = K - 1; t >= 0; --t) {
-                run = min(run, A[t] + pd * (gl * K + t));
-                runa = min(runa, A[t]);
-                sc[t] = run;
-                sa[t] = runa;
-            }
-            incl = run;
-            incla = runa;
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) {
-                const int v = __shfl_down_sync(kFull, incl, o, G);
-                const int va = __shfl_down_sync(kFull, incla, o, G);
-                if (gl + o < G) {
-                    incl = min(incl, v);
-                    incla = min(incla, va);
-                }
-            }
-            excl = __shfl_down_sync(kFull, incl, 1, G);
-            excla = __shfl_down_sync(kFull, incla, 1, G);
-            if (gl == G - 1) excl = excla = kInf;
-#pragma unroll
-            for (int t = 0; t < K; ++t) {
-                sc[t] = min(sc[t], excl);
-                sa[t] = min(sa[t], excla);
-            }
-            const int s = (WIN && act && !first) ? cur_lo - prev_lo : 0;
-            if (WIN && __any_sync(kFull, s != 0)) {
-#pragma unroll
-                for (int t = 0; t < K; ++t) {
-                    pB[gl * K + t + 1] = pb[t];
-                    sC[gl * K + t] = sc[t];
-                    pA[gl * K + t + 1] = pa[t];
-                    sA[gl * K + t] = sa[t];
-                }
-                if (gl == 0) {
-                    pB[0] = pA[0] = kInf;
-                    sC[NJ] = sA[NJ] = kInf;
-                }
-                __syncwarp();
-#pragma unroll
-                for (int t = 0; t < K; ++t) {
-                    const int jj = s + gl * K + t;   // label index in the predecessor window
-                    const int pi = min(max(jj, -1), NJ - 1) + 1;
-                    const int si = min(max(jj, 0), NJ);
-                    int M = min(pu * jj + pB[pi], sC[si] - pd * jj);
-                    M = dbl ? min(M, min(pA[pi] + Tu, sA[si] + T)) : min(M, amin + T);
-                    L[t] = c[t] + M - amin;
-                }
-                __syncwarp();
             } else {
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
-                    const int j = gl * K + t;
-                    int M = min(pu * j + pb[t], sc[t] - pd * j);
-                    M = dbl ? min(M, min(pa[t] + Tu, sa[t] + T)) : min(M, amin + T);
-                    L[t] = c[t] + M - amin;
+                    const int ea = (qr[u][t / 2] >> (16 * (t % 2))) & 0xFFFF;
+                    const int eb = (qr[u][QW + t / 2] >> (16 * (t % 2))) & 0xFFFF;
+                    c[t] = m.in_mode == 1 ? min(ea, eb) : (ea + eb) >> 1;
                 }
             }
-            if (first) {
-#pragma unroll
-                for (int t = 0; t < K; ++t) L[t] = c[t];
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < K; ++t)
-            if (gl * K + t >= Dw) L[t] = 0;
-        if (m.out_mode == 0) {
-            uint16_t *sp = V.S + pix * DWP + gl * K;
-#pragma unroll
-            for (int t = 0; t < K; t += 2)
-                if (act) atomicAdd((unsigned int *)(sp + t), (unsigned)L[t] | ((unsigned)L[t + 1] << 16));
-        } else {
-            int lm = kInf;
 #pragma unroll
             for (int t = 0; t < K; ++t)
-                if (gl * K + t < Dw) lm = min(lm, L[t]);
+                if (gl * K + t >= Dw) c[t] = 0;
+            issue(step + PF, u);
+            bool first = step == 0;
+            if (a.block_cut > 0 && !first &&
+                (x / a.block_cut != (x - dx) / a.block_cut ||
+                 y / a.block_cut != (y - dy) / a.block_cut))
+                first = true;
+            int L[K];
+            if (__all_sync(kFull, first || !act)) {   // every path of the warp starts here
 #pragma unroll
-            for (int o = 1; o < G; o <<= 1) lm = min(lm, __shfl_xor_sync(kFull, lm, o));
-            uint16_t *op = out + pix * DWP + gl * K;
+                for (int t = 0; t < K; ++t) L[t] = c[t];
+            } else {
+                // a path starting here (first pixel or tile edge): L = c below
+                const int P = m.lut ? min(m.lut[abs(cur_i - prev_i)], T) : a.p1;
+                const int pu = dbl ? 2 * P : P, pd = P;
+                int mn = A[0];
 #pragma unroll
-            for (int t = 0; t < K; t += 2) {
-                const unsigned lo16 = gl * K + t < Dw ? (unsigned)(L[t] - lm) : 0u;
-                const unsigned hi16 = gl * K + t + 1 < Dw ? (unsigned)(L[t + 1] - lm) : 0u;
-                if (act) *(unsigned int *)(op + t) = lo16 | (hi16 << 16);
+                for (int t = 1; t < K; ++t) mn = min(mn, A[t]);
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+                const int amin = mn;
+                int pb[K], sc[K], pa[K], sa[K];
+                int run = kInf, runa = kInf;
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    run = min(run, A[t] - pu * (gl * K + t));
+                    runa = min(runa, A[t]);
+                    pb[t] = run;
+                    pa[t] = runa;
+                }
+                int incl = run, incla = runa;
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) {
+                    const int v = __shfl_up_sync(kFull, incl, o, G);
+                    const int va = __shfl_up_sync(kFull, incla, o, G);
+                    if (gl >= o) {
+                        incl = min(incl, v);
+                        incla = min(incla, va);
+                    }
+                }
+                int excl = __shfl_up_sync(kFull, incl, 1, G);
+                int excla = __shfl_up_sync(kFull, incla, 1, G);
+                if (gl == 0) excl = excla = kInf;
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    pb[t] = min(pb[t], excl);
+                    pa[t] = min(pa[t], excla);
+                }
+                run = runa = kInf;
+#pragma unroll
+                for (int t = K - 1; t >= 0; --t) {
+                    run = min(run, A[t] + pd * (gl * K + t));
+                    runa = min(runa, A[t]);
+                    sc[t] = run;
+                    sa[t] = runa;
+                }
+                incl = run;
+                incla = runa;
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) {
+                    const int v = __shfl_down_sync(kFull, incl, o, G);
+                    const int va = __shfl_down_sync(kFull, incla, o, G);
+                    if (gl + o < G) {
+                        incl = min(incl, v);
+                        incla = min(incla, va);
+                    }
+                }
+                excl = __shfl_down_sync(kFull, incl, 1, G);
+                excla = __shfl_down_sync(kFull, incla, 1, G);
+                if (gl == G - 1) excl = excla = kInf;
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    sc[t] = min(sc[t], excl);
+                    sa[t] = min(sa[t], excla);
+                }
+                const int s = (WIN && act && !first) ? cur_lo - prev_lo : 0;
+                if (WIN && __any_sync(kFull, s != 0)) {
+#pragma unroll
+                    for (int t = 0; t < K; ++t) {
+                        pB[gl * K + t + 1] = pb[t];
+                        sC[gl * K + t] = sc[t];
+                        pA[gl * K + t + 1] = pa[t];
+                        sA[gl * K + t] = sa[t];
+                    }
+                    if (gl == 0) {
+                        pB[0] = pA[0] = kInf;
+                        sC[NJ] = sA[NJ] = kInf;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int t = 0; t < K; ++t) {
+                        const int jj = s + gl * K + t;   // label index in the predecessor window
+                        const int pi = min(max(jj, -1), NJ - 1) + 1;
+                        const int si = min(max(jj, 0), NJ);
+                        int M = min(pu * jj + pB[pi], sC[si] - pd * jj);
+                        M = dbl ? min(M, min(pA[pi] + Tu, sA[si] + T)) : min(M, amin + T);
+                        L[t] = c[t] + M - amin;
+                    }
+                    __syncwarp();
+                } else {
+#pragma unroll
+                    for (int t = 0; t < K; ++t) {
+                        const int j = gl * K + t;
+                        int M = min(pu * j + pb[t], sc[t] - pd * j);
+                        M = dbl ? min(M, min(pa[t] + Tu, sa[t] + T)) : min(M, amin + T);
+                        L[t] = c[t] + M - amin;
+                    }
+                }
+                if (first) {
+#pragma unroll
+                    for (int t = 0; t < K; ++t) L[t] = c[t];
+                }
             }
-        }
 #pragma unroll
-        for (int t = 0; t < K; ++t) A[t] = gl * K + t < Dw ? L[t] : kInf;
-        prev_lo = cur_lo;
-        prev_i = cur_i;
+            for (int t = 0; t < K; ++t)
+                if (gl * K + t >= Dw) L[t] = 0;
+            if (m.out_mode == 0) {
+                uint16_t *sp = V.S + pix * DWP + gl * K;
+#pragma unroll
+                for (int t = 0; t < K; t += 2)
+                    if (act)
+                        atomicAdd((unsigned int *)(sp + t),
+                                  (unsigned)L[t] | ((unsigned)L[t + 1] << 16));
+            } else {
+                int lm = kInf;
+#pragma unroll
+                for (int t = 0; t < K; ++t)
+                    if (gl * K + t < Dw) lm = min(lm, L[t]);
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) lm = min(lm, __shfl_xor_sync(kFull, lm, o));
+                uint16_t *op = out + pix * DWP + gl * K;
+#pragma unroll
+                for (int t = 0; t < K; t += 2) {
+                    const unsigned lo16 = gl * K + t < Dw ? (unsigned)(L[t] - lm) : 0u;
+                    const unsigned hi16 = gl * K + t + 1 < Dw ? (unsigned)(L[t + 1] - lm) : 0u;
+                    if (act) *(unsigned int *)(op + t) = lo16 | (hi16 << 16);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < K; ++t) A[t] = gl * K + t < Dw ? L[t] : kInf;
+            prev_lo = cur_lo;
+            prev_i = cur_i;
+        }
     }
 }
 

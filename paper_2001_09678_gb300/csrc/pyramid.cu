@@ -95,12 +95,14 @@ __device__ __forceinline__ uint32_t avg_u16x2(uint32_t a, uint32_t b)
 // Winner-take-all over each pixel's window, ties to the smallest disparity.  Four lanes
 // per pixel; the key (S << 16 | k) orders by energy, then by label.
 
+// LPP lanes per pixel: 4, or 2 for 16-label strides (two 8-label chunks)
+template <int LPP>
 __global__ void wta_kernel(LevelArgs a)
 {
     const int view = blockIdx.z;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = g >> 2;
-    const int sub = (int)(g & 3);
+    const int64_t i = g / LPP;
+    const int sub = (int)(g % LPP);
     const int64_t npx = (int64_t)a.W * a.H;
     const bool in = i < npx;
     const ViewLevel &v = a.v[view];
@@ -110,7 +112,7 @@ __global__ void wta_kernel(LevelArgs a)
         // time, the pixel's 4 lanes consecutive 16-byte chunks
         const uint4 *row = (const uint4 *)(v.S + i * a.Dws);
         const uint4 *row2 = v.S2 ? (const uint4 *)(v.S2 + i * a.Dws) : nullptr;
-        for (int c = sub; c < a.Dws / 8; c += 4) {
+        for (int c = sub; c < a.Dws / 8; c += LPP) {
             uint4 q = row[c];
             if (row2) {   // layered merge: the last layer's two passes, floor of the mean
                 const uint4 q2 = row2[c];
@@ -128,8 +130,8 @@ __global__ void wta_kernel(LevelArgs a)
             }
         }
     }
-    best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 1));
-    best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, 2));
+#pragma unroll
+    for (int o = 1; o < LPP; o <<= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
     const int lo = (in && v.lo) ? (int)v.lo[i] : 0;
     if (in && sub == 0) v.d[i] = (uint16_t)(lo + (best & 0xFFFFu));
 }
@@ -238,9 +240,13 @@ void launch_seed(const SeedArgs &a, cudaStream_t s)
 
 void launch_wta(const LevelArgs &a, cudaStream_t s)
 {
-    const int64_t nthreads = 4 * (int64_t)a.W * a.H;
+    const int lpp = a.Dws >= 32 ? 4 : 2;
+    const int64_t nthreads = lpp * (int64_t)a.W * a.H;
     dim3 grid((unsigned)((nthreads + 255) / 256), 1, a.nviews);
-    wta_kernel<<<grid, 256, 0, s>>>(a);
+    if (lpp == 4)
+        wta_kernel<4><<<grid, 256, 0, s>>>(a);
+    else
+        wta_kernel<2><<<grid, 256, 0, s>>>(a);
     if (a.edge) edge_kernel<<<dim3(kEdgeBlocks, 1, a.nviews), kEdgeThreads, 0, s>>>(a);
 }
 
