@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kScanWarps * 32) agg_general(LevelArgs a, Merg
             for (int t = 0; t < K; ++t) L[t] = c[t];
             first = false;
         } else {
-            const int P = m.lut ? min(m.lut[abs(cur_i - prev_i)], T) : a.p1;
+            const int P = m.lut ? min(m.lut[abs(cur_i - prev_i) & 0xFF], T) : a.p1;
             const int pu = dbl ? 2 * P : P, pd = P;
             int mn = A[0];
 #pragma unroll
@@ -643,8 +643,16 @@ __global__ void __launch_bounds__(kScan8Warps * 32) agg_scan8(LevelArgs a, Merge
 
     // prefetch ring: the data term words, the window start and the intensity of the next
     // PF pixels, loaded PF steps ahead with pinned loads
+    // (zero until loaded: a slot past the end of a short path is never loaded, and its
+    // intensity still indexes the slope table)
     uint32_t qr[PF][2 * QW > 1 ? 2 * QW : 1];
     uint32_t lr[PF], ir[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+        lr[u] = ir[u] = 0u;
+#pragma unroll
+        for (int j = 0; j < (2 * QW > 1 ? 2 * QW : 1); ++j) qr[u][j] = 0u;
+    }
     auto issue = [&](int t, int slot) {
         if (t < n) {
             const int64_t pix = pix0 + t * dpix;
@@ -717,7 +725,7 @@ __global__ void __launch_bounds__(kScan8Warps * 32) agg_scan8(LevelArgs a, Merge
                 for (int t = 0; t < K; ++t) L[t] = c[t];
             } else {
                 // a path starting here (first pixel or tile edge): L = c below
-                const int P = m.lut ? min(m.lut[abs(cur_i - prev_i)], T) : a.p1;
+                const int P = (m.lut && act) ? min(m.lut[abs(cur_i - prev_i) & 0xFF], T) : a.p1;
                 const int pu = dbl ? 2 * P : P, pd = P;
                 int mn = A[0];
 #pragma unroll
