@@ -605,6 +605,50 @@ void launch_general_k(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
 // ---------------------------------------------------------------------------------
 constexpr int kScan8Warps = 4;
 
+// Prefix minima over the path's G lanes of B(j) = A(j) - slope j (j = gl K + t): out[t] =
+// min over labels up to this one; suffix minima of A(j) + slope j likewise from the end.
+template <int K, int G>
+__device__ __forceinline__ void scan8_prefix(const int (&A)[K], int slope, int gl, int (&out)[K])
+{
+    int run = kInf;
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        run = min(run, A[t] - slope * (gl * K + t));
+        out[t] = run;
+    }
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o, G);
+        if (gl >= o) incl = min(incl, v);
+    }
+    int excl = __shfl_up_sync(kFull, incl, 1, G);
+    if (gl == 0) excl = kInf;
+#pragma unroll
+    for (int t = 0; t < K; ++t) out[t] = min(out[t], excl);
+}
+
+template <int K, int G>
+__device__ __forceinline__ void scan8_suffix(const int (&A)[K], int slope, int gl, int (&out)[K])
+{
+    int run = kInf;
+#pragma unroll
+    for (int t = K - 1; t >= 0; --t) {
+        run = min(run, A[t] + slope * (gl * K + t));
+        out[t] = run;
+    }
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        const int v = __shfl_down_sync(kFull, incl, o, G);
+        if (gl + o < G) incl = min(incl, v);
+    }
+    int excl = __shfl_down_sync(kFull, incl, 1, G);
+    if (gl == G - 1) excl = kInf;
+#pragma unroll
+    for (int t = 0; t < K; ++t) out[t] = min(out[t], excl);
+}
+
 template <int K, bool WIN>
 __global__ void __launch_bounds__(kScan8Warps * 32) agg_scan8(LevelArgs a, MergeArgs m)
 {
@@ -734,58 +778,14 @@ __global__ void __launch_bounds__(kScan8Warps * 32) agg_scan8(LevelArgs a, Merge
                 for (int o = 1; o < G; o <<= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
                 const int amin = mn;
                 int pb[K], sc[K], pa[K], sa[K];
-                int run = kInf, runa = kInf;
+                scan8_prefix<K, G>(A, pu, gl, pb);
+                scan8_suffix<K, G>(A, pd, gl, sc);
+                if (dbl) {   // the doubled pass's caps need the running minima of A itself
+                    scan8_prefix<K, G>(A, 0, gl, pa);
+                    scan8_suffix<K, G>(A, 0, gl, sa);
+                } else {
 #pragma unroll
-                for (int t = 0; t < K; ++t) {
-                    run = min(run, A[t] - pu * (gl * K + t));
-                    runa = min(runa, A[t]);
-                    pb[t] = run;
-                    pa[t] = runa;
-                }
-                int incl = run, incla = runa;
-#pragma unroll
-                for (int o = 1; o < G; o <<= 1) {
-                    const int v = __shfl_up_sync(kFull, incl, o, G);
-                    const int va = __shfl_up_sync(kFull, incla, o, G);
-                    if (gl >= o) {
-                        incl = min(incl, v);
-                        incla = min(incla, va);
-                    }
-                }
-                int excl = __shfl_up_sync(kFull, incl, 1, G);
-                int excla = __shfl_up_sync(kFull, incla, 1, G);
-                if (gl == 0) excl = excla = kInf;
-#pragma unroll
-                for (int t = 0; t < K; ++t) {
-                    pb[t] = min(pb[t], excl);
-                    pa[t] = min(pa[t], excla);
-                }
-                run = runa = kInf;
-#pragma unroll
-                for (int t = K - 1; t >= 0; --t) {
-                    run = min(run, A[t] + pd * (gl * K + t));
-                    runa = min(runa, A[t]);
-                    sc[t] = run;
-                    sa[t] = runa;
-                }
-                incl = run;
-                incla = runa;
-#pragma unroll
-                for (int o = 1; o < G; o <<= 1) {
-                    const int v = __shfl_down_sync(kFull, incl, o, G);
-                    const int va = __shfl_down_sync(kFull, incla, o, G);
-                    if (gl + o < G) {
-                        incl = min(incl, v);
-                        incla = min(incla, va);
-                    }
-                }
-                excl = __shfl_down_sync(kFull, incl, 1, G);
-                excla = __shfl_down_sync(kFull, incla, 1, G);
-                if (gl == G - 1) excl = excla = kInf;
-#pragma unroll
-                for (int t = 0; t < K; ++t) {
-                    sc[t] = min(sc[t], excl);
-                    sa[t] = min(sa[t], excla);
+                    for (int t = 0; t < K; ++t) pa[t] = sa[t] = kInf;
                 }
                 const int s = (WIN && act && !first) ? cur_lo - prev_lo : 0;
                 if (WIN && __any_sync(kFull, s != 0)) {
