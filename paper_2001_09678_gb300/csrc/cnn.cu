@@ -306,6 +306,13 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
     const __nv_bfloat16 *src = in + (int64_t)n * (NHWC ? cstr : Cin) * plane;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
     const int K16 = (Cin + 15) / 16 * 16;                // channels the k-steps cover
+    if (NHWC) {
+        // weights already in this layout (zero padding included): 16-byte copies
+        const uint4 *wsrc = (const uint4 *)w;
+        uint4 *wdst = (uint4 *)ws;
+        const int nvec = NC * 9 * CP / 8;
+        for (int i = threadIdx.x; i < nvec; i += 128) wdst[i] = wsrc[i];
+    } else
     // weights: one (co, ci) pair per step, its 9 taps contiguous in global memory;
     // output channels Cout .. NC-1 have zero weights
     for (int i0 = threadIdx.x; i0 < NC * Cin; i0 += 256) {   // two pairs per round
@@ -330,8 +337,9 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(
     }
     // channels Cin .. K16-1 are zero in both operands (never rewritten below)
     const int npad = K16 - Cin;
-    for (int i = threadIdx.x; i < NC * 9 * npad; i += 128)
-        ws[(i / npad) * CP + Cin + i % npad] = zero;
+    if (!NHWC)
+        for (int i = threadIdx.x; i < NC * 9 * npad; i += 128)
+            ws[(i / npad) * CP + Cin + i % npad] = zero;
     for (int i = threadIdx.x; i < TR * TC * npad; i += 128)
         xs[(i / npad) * CP + Cin + i % npad] = zero;
 
@@ -469,7 +477,7 @@ void launch_mma(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
                 float *out_f, cudaStream_t s)
 {
     // channel stride: Cin rounded up to 16 (whole k-steps) plus 8 (bank spread)
-    const int CP = (Cin + 15) / 16 * 16 + 8;
+    const int CP = mma_channel_stride(Cin);
     const int NC = Cout == 32 ? 32 : 8;
     const size_t smem =
         sizeof(__nv_bfloat16) * (size_t)CP * ((kMmaRows + 2) * (kMmaCols + 2) + NC * 9);

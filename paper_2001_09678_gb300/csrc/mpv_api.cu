@@ -677,18 +677,42 @@ mpv_status mpv_load_proposal_weights(mpv_ctx *ctx, const char *path)
         iw += n;
         ib += net.cout[k];
     }
+    // the same weights in the tensor-core kernel's shared-memory layout, [NC][9][CP]
+    // (zero-padded output and input channels), copied whole by the matcher's network
+    std::vector<__nv_bfloat16> ht;
+    size_t toff[kProposalLayers];
+    {
+        size_t iw2 = 0;
+        const __nv_bfloat16 zero = __float2bfloat16(0.f);
+        for (int k = 0; k < kProposalLayers; ++k) {
+            const int Cin = net.cin[k], Cout = net.cout[k];
+            const int NC = Cout == 32 ? 32 : 8, CP = mma_channel_stride(Cin);
+            toff[k] = ht.size();
+            ht.resize(ht.size() + (size_t)NC * 9 * CP, zero);
+            for (int co = 0; co < Cout; ++co)
+                for (int c = 0; c < Cin; ++c)
+                    for (int tap = 0; tap < 9; ++tap)
+                        ht[toff[k] + ((size_t)co * 9 + tap) * CP + c] =
+                            hw[iw2 + ((size_t)co * Cin + c) * 9 + tap];
+            iw2 += (size_t)Cout * Cin * 9;
+        }
+    }
+    const size_t bbytes = ((nb * sizeof(float)) + 255) & ~(size_t)255;
     DeviceGuard guard(ctx->device);
     void *mem = nullptr;
-    if (cudaMalloc(&mem, wbytes + nb * sizeof(float)) != cudaSuccess) {
+    if (cudaMalloc(&mem, wbytes + bbytes + ht.size() * sizeof(__nv_bfloat16)) != cudaSuccess) {
         cudaGetLastError();
         return MPV_ERR_OOM;
     }
     cudaMemcpy(mem, hw.data(), nw * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
     cudaMemcpy((uint8_t *)mem + wbytes, hb.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy((uint8_t *)mem + wbytes + bbytes, ht.data(), ht.size() * sizeof(__nv_bfloat16),
+               cudaMemcpyHostToDevice);
     iw = ib = 0;
     for (int k = 0; k < kProposalLayers; ++k) {
         net.w[k] = (const __nv_bfloat16 *)mem + iw;
         net.b[k] = (const float *)((uint8_t *)mem + wbytes) + ib;
+        net.wt[k] = (const __nv_bfloat16 *)((uint8_t *)mem + wbytes + bbytes) + toff[k];
         iw += (size_t)net.cout[k] * net.cin[k] * 9;
         ib += net.cout[k];
     }

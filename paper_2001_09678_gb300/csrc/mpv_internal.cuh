@@ -118,6 +118,7 @@ struct ProposalNet {
     int cin[kProposalLayers], cout[kProposalLayers], relu[kProposalLayers];
     const void *w[kProposalLayers];     // __nv_bfloat16 [cout][cin][3][3]
     const float *b[kProposalLayers];
+    const void *wt[kProposalLayers];    // the same in the tensor-core kernel's layout
     int train_D = 0, factor = 0;
 };
 
@@ -130,9 +131,12 @@ void launch_features(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const
 void launch_features_nhwc(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const uint8_t *C,
                           int Dws, int Dw, int W, int H, int cstr, __nv_bfloat16 *out,
                           cudaStream_t s);
+// wt: the weights laid out [NC][9][mma_channel_stride(Cin)] (NC = 32, or 8 for Cout = 1)
 void launch_conv3x3_nhwc(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
-                         const __nv_bfloat16 *w, const float *b, int Cout, int relu,
+                         const __nv_bfloat16 *wt, const float *b, int Cout, int relu,
                          __nv_bfloat16 *out_bf, float *out_f, cudaStream_t s);
+// channel stride of the tensor-core convolution's shared tiles: whole k-steps plus 8
+inline int mma_channel_stride(int Cin) { return (Cin + 15) / 16 * 16 + 8; }
 // channels per pixel of the network input in the matcher's buffers
 inline int feature_stride(int Dw_top) { return (2 + Dw_top + 7) / 8 * 8; }
 void launch_proposal_windows(const float *q, int Wq, int Hq, int f, int W, int H, int D, int Dw,

@@ -311,7 +311,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             for (int k = 0; k < net->layers; ++k) {
                 const bool lastk = k + 1 == net->layers;
                 launch_conv3x3_nhwc(in, nviews, net->cin[k], cstr, a.H, a.W,
-                                    (const __nv_bfloat16 *)net->w[k], net->b[k], net->cout[k],
+                                    (const __nv_bfloat16 *)net->wt[k], net->b[k], net->cout[k],
                                     net->relu[k], lastk ? nullptr : bufs[k & 1],
                                     lastk ? (float *)(base + L.q) : nullptr, s);
                 in = bufs[k & 1];
