@@ -107,12 +107,28 @@ __global__ void __launch_bounds__(kRoadThreads) road_kernel(const uint32_t *__re
                 for (int j = threadIdx.x; j < H; j += kRoadThreads) {
                     int32_t best = -1;
                     int arg = 0;
-                    // ascending predecessors, strict comparison: ties to the smaller row
-                    for (int jp = max(0, j - eta + 1); jp < j; ++jp) {
-                        const int32_t v = prev[jp];
-                        if (v > best) {
-                            best = v;
-                            arg = jp;
+                    // predecessors in chunks of 8 loaded together, each chunk reduced as a
+                    // tree; the earlier (smaller) row wins ties inside a chunk and between
+                    // chunks (strict comparison against the running best)
+                    for (int j0 = max(0, j - eta + 1); j0 < j; j0 += 8) {
+                        int32_t v[8];
+                        int ix[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            ix[e] = j0 + e;
+                            v[e] = j0 + e < j ? prev[j0 + e] : -2;
+                        }
+#pragma unroll
+                        for (int w = 1; w < 8; w <<= 1)
+#pragma unroll
+                            for (int e = 0; e < 8; e += 2 * w)
+                                if (v[e + w] > v[e]) {
+                                    v[e] = v[e + w];
+                                    ix[e] = ix[e + w];
+                                }
+                        if (v[0] > best) {
+                            best = v[0];
+                            arg = ix[0];
                         }
                     }
                     cur[j] = best < 0 ? -1 : best + (int32_t)chunk[c * H + j];
