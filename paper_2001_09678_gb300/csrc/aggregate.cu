@@ -120,10 +120,36 @@ __device__ __forceinline__ int path_length(int dx, int dy, int W, int H, int x0,
 // RM (ceil(T/p1) - 1 <= RM) the stencil min over |d| <= RM plus the cap min_v A(v) + T
 // is the full-connectivity minimum.  WIN: the level has per-pixel windows, and the
 // predecessor is re-indexed into the current window through shared memory every step.
+// floor((a + b) / 2) of each 16-bit half (the shift masked so that no bit crosses
+// from the high half into the low half)
+__device__ __forceinline__ uint32_t avg_u16x2(uint32_t a, uint32_t b)
+{
+    return (a & b) + (((a ^ b) >> 1) & 0x7FFF7FFFu);
+}
+
+// Packed energies of one lane minus the path's minimum m2 (both halves), padding labels
+// as 0, stored as KW 32-bit words.
+template <int KW>
+__device__ __forceinline__ void store_normalised(uint16_t *dst, const uint32_t (&A)[KW], uint32_t m2,
+                                                 const uint32_t (&keep)[KW], bool padded)
+{
+#pragma unroll
+    for (int i = 0; i < KW; ++i) {
+        uint32_t v = A[i] - m2;           // per half: A >= m2 on every kept label
+        if (padded) v &= keep[i];
+        ((uint32_t *)dst)[i] = v;
+    }
+}
+
 // BLK: the level is split into independent block_cut x block_cut tiles (a scan path
 // restarts where it enters a new tile); counters track the steps to the next tile edge.
-template <int G, int KW, int RM, bool WIN, bool BLK>
-__global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
+// LAYER: one layer of the paper's layered merge - the data term is the cost bytes
+// (mg.in_mode 0) or the previous layer's two passes merged by min (1) or floor mean (2),
+// and the pass stores its per-pixel min-normalised energies into its own volume instead
+// of adding into S (one step late, when the next step's minimum over the path's labels
+// is known).
+template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER>
+__global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, MergeArgs mg)
 {
     constexpr int kG = G;                    // lanes per scan path
     constexpr int kPathsPerWarp = 32 / kG;
@@ -138,7 +164,12 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
 
     __shared__ __align__(16) uint16_t rbuf[WIN ? kStencilWarps * kPathsPerWarp * BUF : 8];
 
-    const int view = blockIdx.z, dir = blockIdx.y;
+    const int view = blockIdx.z, dir = mg.dir0 + blockIdx.y;
+    // layered merge: the previous layer's pair (IN) and this pass's own volume (OUTN)
+    const uint16_t *qa = view ? mg.qa[1] : mg.qa[0];
+    const uint16_t *qb = view ? mg.qb[1] : mg.qb[0];
+    uint16_t *const *outs = view ? mg.out[1] : mg.out[0];
+    uint16_t *const outv = (dir & 1) ? outs[1] : outs[0];
     const int dx = c_dirs[dir][0], dy = c_dirs[dir][1];
     const int W = a.W, H = a.H, Dw = a.Dw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -179,14 +210,38 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
     uint16_t *sbase = V.S + gl * K;
     const uint16_t *lob = V.lo;
 
-    // prefetch ring (registers): cost bytes and window start of the next PF steps
+    // prefetch ring (registers): cost bytes (or the previous layer's two words per
+    // packed pair) and window start of the next PF steps
+    constexpr int QW = LAYER ? KW : 1;
+    const int IN = LAYER ? mg.in_mode : 0;
+    constexpr bool OUTN = LAYER;
     uint32_t cq[PF][CW];
+    uint32_t qaq[PF][QW], qbq[PF][QW];
     uint32_t lq[PF];
     auto issue = [&](int t, int slot) {
         if (t < n) {
             const int pix = pix0 + t * dpix;
             const uint8_t *src = cbase + (int64_t)pix * DWP;
-            if (KW == 1) {
+            if (LAYER && IN) {
+                const uint16_t *sa = qa + (int64_t)pix * DWP + gl * K;
+                const uint16_t *sb = qb + (int64_t)pix * DWP + gl * K;
+                if (KW % 2 == 0) {
+#pragma unroll
+                    for (int j = 0; j < KW; j += 2) {
+                        const uint2 va = ld_pin_u64(sa + 2 * j), vb = ld_pin_u64(sb + 2 * j);
+                        qaq[slot][j % QW] = va.x;
+                        qaq[slot][(j + 1) % QW] = va.y;
+                        qbq[slot][j % QW] = vb.x;
+                        qbq[slot][(j + 1) % QW] = vb.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < KW; ++j) {
+                        qaq[slot][j % QW] = ld_pin_u32(sa + 2 * j);
+                        qbq[slot][j % QW] = ld_pin_u32(sb + 2 * j);
+                    }
+                }
+            } else if (KW == 1) {
                 cq[slot][0] = ld_pin_u16(src);
             } else if (CW % 2 == 0) {
 #pragma unroll
@@ -227,7 +282,12 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
             const bool act = t < n;
             const int pix = pix0 + t * dpix;
             uint32_t c[KW];
-            if (KW == 1) {
+            if (LAYER && IN) {
+#pragma unroll
+                for (int i = 0; i < KW; ++i)
+                    c[i] = IN == 1 ? __vminu2(qaq[u][i % QW], qbq[u][i % QW])
+                                   : avg_u16x2(qaq[u][i % QW], qbq[u][i % QW]);
+            } else if (KW == 1) {
                 c[0] = __byte_perm(cq[u][0], 0u, 0x4140);
             } else {
 #pragma unroll
@@ -239,6 +299,16 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
             const int cur_lo = (int)lq[u];
             issue(t + PF, u);
 
+            // minimum of the predecessor over the path's lanes, in both halves
+            uint32_t m2 = A[0];
+#pragma unroll
+            for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
+            m2 = __vminu2(m2, __byte_perm(m2, m2, 0x1032));
+#pragma unroll
+            for (int o = 1; o < kG; o <<= 1) m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, o));
+            if (OUTN && t > 0 && t - 1 < n)   // the previous pixel, normalised by its minimum
+                store_normalised<KW>(outv + (int64_t)(pix - dpix) * DWP + gl * K, A, m2, keep,
+                                     padded);
             if (BLK && t > 0) {   // entering a new tile: the path starts again here
                 --cx;
                 --cy;
@@ -248,15 +318,9 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
                 if (cut) {
 #pragma unroll
                     for (int i = 0; i < KW; ++i) A[i] = INF2;
+                    m2 = INF2;
                 }
             }
-            // minimum of the predecessor over the path's lanes, in both halves
-            uint32_t m2 = A[0];
-#pragma unroll
-            for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
-            m2 = __vminu2(m2, __byte_perm(m2, m2, 0x1032));
-#pragma unroll
-            for (int o = 1; o < kG; o <<= 1) m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, o));
             const uint32_t cap = m2 + Tx2;
 
             // predecessor words around this lane's labels, HW halo words per side
@@ -317,7 +381,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
                 }
                 c[i] = L;
             }
-            if (act) {
+            if (act && !OUTN) {
                 if (KW % 2 == 0) {
                     unsigned long long *sp = (unsigned long long *)(sbase + (int64_t)pix * DWP);
 #pragma unroll
@@ -332,15 +396,27 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a)
             prev_lo = cur_lo;
         }
     }
+    if (OUTN) {   // the last pixel of the longest paths: nothing follows to store it
+        uint32_t m2 = A[0];
+#pragma unroll
+        for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
+        m2 = __vminu2(m2, __byte_perm(m2, m2, 0x1032));
+#pragma unroll
+        for (int o = 1; o < kG; o <<= 1) m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, o));
+        if (n > 0 && n == nmax)
+            store_normalised<KW>(outv + (int64_t)(pix0 + (n - 1) * dpix) * DWP + gl * K, A, m2,
+                                 keep, padded);
+    }
 }
 
-template <int G, int KW, int RM, bool WIN, bool BLK>
-void launch_stencil(const LevelArgs &a, cudaStream_t s)
+template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER = false>
+void launch_stencil(const LevelArgs &a, cudaStream_t s, const MergeArgs &mg = MergeArgs{},
+                    int ndirs = 0)
 {
     const int maxp = a.W + a.H - 1;
     const int per_block = kStencilWarps * (32 / G);
-    dim3 grid((maxp + per_block - 1) / per_block, a.npaths, a.nviews);
-    agg_stencil<G, KW, RM, WIN, BLK><<<grid, kStencilWarps * 32, 0, s>>>(a);
+    dim3 grid((maxp + per_block - 1) / per_block, ndirs ? ndirs : a.npaths, a.nviews);
+    agg_stencil<G, KW, RM, WIN, BLK, LAYER><<<grid, kStencilWarps * 32, 0, s>>>(a, mg);
 }
 
 // windows (pyramid levels below the top) and tiles (the top level only) never meet
@@ -886,6 +962,67 @@ void launch_aggregate_general(const LevelArgs &a, const MergeArgs &m, cudaStream
     else if (K <= 8) launch_general_k<8>(a, m, s);
     else if (K <= 16) launch_general_k<16>(a, m, s);
     else launch_general_k<32>(a, m, s);
+}
+
+// ---------------------------------------------------------------------------------
+// One layer of the layered merge: the packed stencil where its arithmetic holds (jumps
+// beyond 4 labels truncated, no gradient table, strides of 16 or 32 labels, energies far
+// below the packed sentinel), the doubled left-to-right pass and everything else through
+// the general kernels.
+// ---------------------------------------------------------------------------------
+namespace {
+
+bool layer_stencil_ok(const LevelArgs &a, const MergeArgs &m)
+{
+    return m.out_mode == 1 && !m.lut && a.radius <= 4 && (a.Dws == 16 || a.Dws == 32) &&
+           255 + 10 * a.trunc < (int)kInf16;
+}
+
+template <int G, int KW>
+void launch_layer_kw(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
+{
+    const bool win = a.v[0].lo != nullptr;
+    const bool blk = a.block_cut > 0;
+    if (a.radius <= 2) {
+        if (win) launch_stencil<G, KW, 2, true, false, true>(a, s, m, m.ndirs);
+        else if (blk) launch_stencil<G, KW, 2, false, true, true>(a, s, m, m.ndirs);
+        else launch_stencil<G, KW, 2, false, false, true>(a, s, m, m.ndirs);
+    } else if constexpr (KW >= 2) {
+        if (win) launch_stencil<G, KW, 4, true, false, true>(a, s, m, m.ndirs);
+        else if (blk) launch_stencil<G, KW, 4, false, true, true>(a, s, m, m.ndirs);
+        else launch_stencil<G, KW, 4, false, false, true>(a, s, m, m.ndirs);
+    }
+}
+
+void launch_layer_stencil(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
+{
+    if (a.Dws == 32) launch_layer_kw<kLanesWide, 2>(a, m, s);
+    else if (a.radius <= 2) launch_layer_kw<kLanesWide, 1>(a, m, s);
+    else launch_layer_kw<4, 2>(a, m, s);
+}
+
+}  // namespace
+
+int launch_layer(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
+{
+    if (!layer_stencil_ok(a, m)) {
+        launch_aggregate_general(a, m, s);
+        return 1;
+    }
+    const bool dbl = m.double_up_dir >= m.dir0 && m.double_up_dir < m.dir0 + m.ndirs;
+    if (!dbl) {
+        launch_layer_stencil(a, m, s);
+        return 1;
+    }
+    // the doubled pass needs the asymmetric caps of the general kernels
+    for (int d = m.dir0; d < m.dir0 + m.ndirs; ++d) {
+        MergeArgs one = m;
+        one.dir0 = d;
+        one.ndirs = 1;
+        if (d == m.double_up_dir) launch_aggregate_general(a, one, s);
+        else launch_layer_stencil(a, one, s);
+    }
+    return m.ndirs;
 }
 
 void launch_aggregate(const LevelArgs &a, cudaStream_t s)

@@ -91,6 +91,8 @@ struct MergeArgs {
     uint16_t *out[kMaxViews][2];
 };
 void launch_aggregate_general(const LevelArgs &a, const MergeArgs &m, cudaStream_t s);
+// one layer of the layered merge (out_mode 1); returns the number of launches
+int launch_layer(const LevelArgs &a, const MergeArgs &m, cudaStream_t s);
 void launch_wta(const LevelArgs &a, cudaStream_t s);
 void launch_lr(const uint16_t *dL, const uint16_t *dRm, int W, int H, int tol, int check,
                uint16_t *out, int out_pitch, uint16_t *out_right, int right_pitch,

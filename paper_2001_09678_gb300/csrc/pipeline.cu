@@ -348,7 +348,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
                     m.out[v][0] = B[v][out];
                     m.out[v][1] = B[v][out + 1];
                 }
-                launch_aggregate_general(a, m, s);
+                launch_layer(a, m, s);
             }
             for (int v = 0; v < nviews; ++v) {
                 a.v[v].S = B[v][2];

@@ -93,6 +93,12 @@ CASES = {
     "paper_grad_s3": (lambda: synth.slanted_pair(224, 128, seed=49, d_max=56)[:2],
                       dict(max_disparity=64, num_scales=3, num_paths=8, merge_mode=PAPER),
                       exp_table(10, 16)),
+    "paper_radius4_s2": (lambda: synth.slanted_pair(192, 112, seed=75, d_max=40)[:2],
+                         dict(max_disparity=48, num_scales=2, num_paths=8, p1=10, trunc=45,
+                              window=12, merge_mode=PAPER), None),
+    "paper_tiles_s3": (lambda: synth.slanted_pair(224, 128, seed=76, d_max=56)[:2],
+                       dict(max_disparity=64, num_scales=3, num_paths=8, merge_mode=PAPER,
+                            top_block=9), None),
     # the top level split into independent tiles (Section 3.4 read literally)
     "tiles_s3_b16": (lambda: synth.slanted_pair(256, 160, seed=70, d_max=60)[:2],
                      dict(max_disparity=64, num_scales=3, num_paths=8, top_block=16), None),
