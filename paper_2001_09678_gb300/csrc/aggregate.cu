@@ -19,13 +19,14 @@
 //    32-bit register; the stencil is packed 16-bit add-min arithmetic, the halo words
 //    come from the neighbouring lanes by shuffles, and a window shift between
 //    consecutive pixels (pyramid levels) re-indexes the predecessor through shared
-//    memory.  S is accumulated with 64-bit reductions of four packed labels.
+//    memory.  S is accumulated with 64-bit reductions of four packed labels.  In its
+//    layer mode it runs one layer of the paper's layered merge (Section 3.2), the
+//    left-to-right pass with doubled upward jumps included.
 //  * agg_general: any R and window width: one warp per scan path, the two sweeps written
 //    as prefix minima  min_{v<=u} A(v) + p1 (u-v) = p1 u + min_{v<=u} (A(v) - p1 v)
 //    (and the mirror image), evaluated by shuffle scans over the lanes.  It also runs
-//    the variants: a slope per step from the image gradient (Eq. EU) and the paper's
-//    layered merge of Section 3.2 (passes stored per direction and merged by the next
-//    layer, the left-to-right pass with doubled upward jumps).
+//    the variants the stencil cannot: a slope per step from the image gradient (Eq. EU),
+//    and the layered merge at radii or widths outside the stencil's.
 #include "mpv_internal.cuh"
 
 namespace mpv {
@@ -147,7 +148,13 @@ __device__ __forceinline__ void store_normalised(uint16_t *dst, const uint32_t (
 // (mg.in_mode 0) or the previous layer's two passes merged by min (1) or floor mean (2),
 // and the pass stores its per-pixel min-normalised energies into its own volume instead
 // of adding into S (one step late, when the next step's minimum over the path's labels
-// is known).
+// is known).  The pass mg.double_up_dir charges upward jumps twice (u > v: 2 min(p1 d, T));
+// its envelope is
+//     M'(u) = min( A(u), min_{1<=d<=RM} A(u-d) + 2 min(p1 d, T), A(u+d) + min(p1 d, T),
+//                  min_v A(v) + 2T,  min_{v>=u} A(v) + T ),
+// exact because every added term is at least one true term and every jump beyond RM is
+// covered (upward ones by min_v A(v) + 2T, downward ones by the suffix minimum + T).  The
+// suffix minimum is a packed scan over the lane's words and the path's lanes.
 template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER>
 __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, MergeArgs mg)
 {
@@ -163,6 +170,9 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     constexpr int CW = KW >= 2 ? KW / 2 : 1; // 32-bit words of cost bytes per lane
 
     __shared__ __align__(16) uint16_t rbuf[WIN ? kStencilWarps * kPathsPerWarp * BUF : 8];
+    // suffix minima of the predecessor for the doubled pass: lower pad = the path's
+    // minimum (every predecessor label lies above), upper pad absent
+    __shared__ __align__(16) uint16_t sbuf[WIN && LAYER ? kStencilWarps * kPathsPerWarp * BUF : 8];
 
     const int view = blockIdx.z, dir = mg.dir0 + blockIdx.y;
     // layered merge: the previous layer's pair (IN) and this pass's own volume (OUTN)
@@ -178,8 +188,11 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     const ViewLevel &V = a.v[view];
 
     uint16_t *gb = rbuf + (WIN ? (warp * kPathsPerWarp + grp) * BUF : 0);
+    uint16_t *sb = sbuf + (WIN && LAYER ? (warp * kPathsPerWarp + grp) * BUF : 0);
     if (WIN) {
         for (int i = gl; i < BUF; i += kG) gb[i] = (uint16_t)kInf16;
+        if (LAYER)
+            for (int i = gl; i < BUF; i += kG) sb[i] = (uint16_t)kInf16;
         __syncwarp();
     }
 
@@ -188,6 +201,11 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     const uint32_t Tx2 = T * 0x10001u;
     const uint32_t E1 = min(P1, T) * 0x10001u, E2 = min(2 * P1, T) * 0x10001u;
     const uint32_t E3 = min(3 * P1, T) * 0x10001u, E4 = min(4 * P1, T) * 0x10001u;
+    // the doubled pass (block-uniform): upward jumps and their cap cost twice
+    const bool asym = LAYER && dir == mg.double_up_dir;
+    const uint32_t up = asym ? 2u : 1u;
+    const uint32_t U1 = E1 * up, U2 = E2 * up, U3 = E3 * up, U4 = E4 * up;
+    const uint32_t Tcap = Tx2 * up;
 
     // labels at or beyond Dw are padding: never a predecessor, never summed
     const bool padded = Dw < DWP;
@@ -304,6 +322,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
 #pragma unroll
             for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
             m2 = __vminu2(m2, __byte_perm(m2, m2, 0x1032));
+            uint32_t lm = m2;                 // this lane's minimum
 #pragma unroll
             for (int o = 1; o < kG; o <<= 1) m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, o));
             if (OUTN && t > 0 && t - 1 < n)   // the previous pixel, normalised by its minimum
@@ -319,9 +338,29 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
 #pragma unroll
                     for (int i = 0; i < KW; ++i) A[i] = INF2;
                     m2 = INF2;
+                    lm = INF2;
                 }
             }
-            const uint32_t cap = m2 + Tx2;
+            const uint32_t cap = m2 + Tcap;
+
+            // doubled pass: suffix minima SA(u) = min_{v>=u} A(v), first over the lanes
+            // above (exclusive scan of the lane minima), then down the lane's own words
+            uint32_t SA[KW];
+            if (asym) {
+                uint32_t ex = __shfl_down_sync(kFull, lm, 1, kG);
+                if (gl == kG - 1) ex = INF2;
+#pragma unroll
+                for (int o = 1; o < kG; o <<= 1) {
+                    const uint32_t v = __shfl_down_sync(kFull, ex, o, kG);
+                    if (gl + o < kG) ex = __vminu2(ex, v);
+                }
+#pragma unroll
+                for (int i = KW - 1; i >= 0; --i) {
+                    const uint32_t v = __vminu2(A[i], ex);               // (min(lo,r), min(hi,r))
+                    SA[i] = __vminu2(v, __byte_perm(v, v, 0x3232));     // low half also <= high
+                    ex = __byte_perm(SA[i], SA[i], 0x1010);
+                }
+            }
 
             // predecessor words around this lane's labels, HW halo words per side
             uint32_t E[NE];
@@ -341,6 +380,13 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                 uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
 #pragma unroll
                 for (int i = 0; i < KW; ++i) gw[i] = A[i];
+                if (LAYER && asym) {
+                    uint32_t *sw = (uint32_t *)(sb + PAD + gl * K);
+#pragma unroll
+                    for (int i = 0; i < KW; ++i) sw[i] = SA[i];
+                    uint32_t *sl = (uint32_t *)(sb + PAD - DWP);
+                    for (int w = gl; w < DWP / 2; w += kG) sl[w] = m2;
+                }
                 __syncwarp();
                 const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
                 const int j0 = PAD + gl * K - 2 * HW + sc;
@@ -351,6 +397,19 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                 for (int i = 0; i <= NE; ++i) Wd[i] = gwords[i];
 #pragma unroll
                 for (int w = 0; w < NE; ++w) E[w] = __byte_perm(Wd[w], Wd[w + 1], sel);
+                if (LAYER && asym) {
+                    // current label j reads the predecessor's suffix minimum at j + s:
+                    // below its window every label is above (the minimum), beyond it none
+                    const int s2 = min(max(s, -DWP), DWP);
+                    const int j1 = PAD + gl * K + s2;
+                    const uint32_t *swords = (const uint32_t *)sb + (j1 >> 1);
+                    const uint32_t sel2 = (j1 & 1) ? 0x5432u : 0x3210u;
+                    uint32_t Sd[KW + 1];
+#pragma unroll
+                    for (int i = 0; i <= KW; ++i) Sd[i] = swords[i];
+#pragma unroll
+                    for (int i = 0; i < KW; ++i) SA[i] = __byte_perm(Sd[i], Sd[i + 1], sel2);
+                }
                 __syncwarp();
             }
 
@@ -361,17 +420,19 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
 #pragma unroll
             for (int i = 0; i < KW; ++i) {
                 const int e = HW + i;
+                // words below e hold smaller labels: jumps up into (u, u+1)
                 uint32_t m = __vminu2(E[e], cap);
-                m = __viaddmin_u16x2(SH[e - 1], E1, m);
+                m = __viaddmin_u16x2(SH[e - 1], U1, m);
                 m = __viaddmin_u16x2(SH[e], E1, m);
-                m = __viaddmin_u16x2(E[e - 1], E2, m);
+                m = __viaddmin_u16x2(E[e - 1], U2, m);
                 m = __viaddmin_u16x2(E[e + 1], E2, m);
                 if (RM >= 4) {
-                    m = __viaddmin_u16x2(SH[e - 2], E3, m);
+                    m = __viaddmin_u16x2(SH[e - 2], U3, m);
                     m = __viaddmin_u16x2(SH[e + 1], E3, m);
-                    m = __viaddmin_u16x2(E[e - 2], E4, m);
+                    m = __viaddmin_u16x2(E[e - 2], U4, m);
                     m = __viaddmin_u16x2(E[e + 2], E4, m);
                 }
+                if (asym) m = __viaddmin_u16x2(SA[i], Tx2, m);
                 uint32_t L = c[i] + m - m2;      // per half: no carry, no borrow
                 if (padded) {
                     L &= keep[i];
@@ -1009,20 +1070,8 @@ int launch_layer(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
         launch_aggregate_general(a, m, s);
         return 1;
     }
-    const bool dbl = m.double_up_dir >= m.dir0 && m.double_up_dir < m.dir0 + m.ndirs;
-    if (!dbl) {
-        launch_layer_stencil(a, m, s);
-        return 1;
-    }
-    // the doubled pass needs the asymmetric caps of the general kernels
-    for (int d = m.dir0; d < m.dir0 + m.ndirs; ++d) {
-        MergeArgs one = m;
-        one.dir0 = d;
-        one.ndirs = 1;
-        if (d == m.double_up_dir) launch_aggregate_general(a, one, s);
-        else launch_layer_stencil(a, one, s);
-    }
-    return m.ndirs;
+    launch_layer_stencil(a, m, s);   // the doubled pass included (asymmetric stencil)
+    return 1;
 }
 
 void launch_aggregate(const LevelArgs &a, cudaStream_t s)

@@ -96,6 +96,9 @@ CASES = {
     "paper_radius4_s2": (lambda: synth.slanted_pair(192, 112, seed=75, d_max=40)[:2],
                          dict(max_disparity=48, num_scales=2, num_paths=8, p1=10, trunc=45,
                               window=12, merge_mode=PAPER), None),
+    "paper_d128_s3_w32": (lambda: synth.slanted_pair(288, 160, seed=77, d_max=110)[:2],
+                          dict(max_disparity=128, num_scales=3, num_paths=8, merge_mode=PAPER),
+                          None),
     "paper_tiles_s3": (lambda: synth.slanted_pair(224, 128, seed=76, d_max=56)[:2],
                        dict(max_disparity=64, num_scales=3, num_paths=8, merge_mode=PAPER,
                             top_block=9), None),
