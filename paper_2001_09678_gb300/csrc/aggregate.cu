@@ -155,7 +155,17 @@ __device__ __forceinline__ void store_normalised(uint16_t *dst, const uint32_t (
 // exact because every added term is at least one true term and every jump beyond RM is
 // covered (upward ones by min_v A(v) + 2T, downward ones by the suffix minimum + T).  The
 // suffix minimum is a packed scan over the lane's words and the path's lanes.
-template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER>
+// SWP: the slope of each step comes from the gradient table (Eq. EU's weighting,
+// lut[|I0(p) - I0(p-r)|]), so no fixed radius holds; the two sweeps of Section 3.3 are then
+// evaluated untruncated in packed form,
+//     F(u) = min_{v<=u} A(v) + pu (u-v),   G(u) = min_{v>=u} A(v) + pd (v-u),
+// inside the lane by doubling (one label, then whole words) and across the path's lanes by
+// a scan of the lanes' end values, and M'(u) = min(F(u), G(u), min_v A(v) + T) (plus the
+// doubled pass's suffix term).  Sweep values never exceed the sentinel plus pu times the
+// labels of a lane, which the dispatch keeps below 2^16.  With windows, the envelope is
+// formed in the predecessor's frame and re-indexed; labels beyond the predecessor's window
+// continue the sweeps linearly from its edge, capped.
+template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER, bool SWP>
 __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, MergeArgs mg)
 {
     constexpr int kG = G;                    // lanes per scan path
@@ -172,7 +182,12 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     __shared__ __align__(16) uint16_t rbuf[WIN ? kStencilWarps * kPathsPerWarp * BUF : 8];
     // suffix minima of the predecessor for the doubled pass: lower pad = the path's
     // minimum (every predecessor label lies above), upper pad absent
-    __shared__ __align__(16) uint16_t sbuf[WIN && LAYER ? kStencilWarps * kPathsPerWarp * BUF : 8];
+    __shared__ __align__(16) uint16_t sbuf[WIN && LAYER && !SWP ? kStencilWarps * kPathsPerWarp * BUF : 8];
+    __shared__ int slut[SWP ? 256 : 1];      // the gradient table's slopes
+    if (SWP) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) slut[i] = mg.lut[i];
+        __syncthreads();
+    }
 
     const int view = blockIdx.z, dir = mg.dir0 + blockIdx.y;
     // layered merge: the previous layer's pair (IN) and this pass's own volume (OUTN)
@@ -188,10 +203,10 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     const ViewLevel &V = a.v[view];
 
     uint16_t *gb = rbuf + (WIN ? (warp * kPathsPerWarp + grp) * BUF : 0);
-    uint16_t *sb = sbuf + (WIN && LAYER ? (warp * kPathsPerWarp + grp) * BUF : 0);
+    uint16_t *sb = sbuf + (WIN && LAYER && !SWP ? (warp * kPathsPerWarp + grp) * BUF : 0);
     if (WIN) {
         for (int i = gl; i < BUF; i += kG) gb[i] = (uint16_t)kInf16;
-        if (LAYER)
+        if (LAYER && !SWP)
             for (int i = gl; i < BUF; i += kG) sb[i] = (uint16_t)kInf16;
         __syncwarp();
     }
@@ -236,6 +251,12 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     uint32_t cq[PF][CW];
     uint32_t qaq[PF][QW], qbq[PF][QW];
     uint32_t lq[PF];
+    // SWP: the reference intensity of the next PF pixels (zero until loaded: a slot past
+    // the end of a short path is never loaded)
+    uint32_t iq[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) iq[u] = 0u;
+    const int64_t ipix0 = (int64_t)y0 * V.pitch0 + x0, dipix = (int64_t)dy * V.pitch0 + dx;
     auto issue = [&](int t, int slot) {
         if (t < n) {
             const int pix = pix0 + t * dpix;
@@ -273,6 +294,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                 for (int j = 0; j < CW; ++j) cq[slot][j] = ld_pin_u32(src + 4 * j);
             }
             lq[slot] = WIN ? ld_pin_u16(lob + pix) : 0u;
+            if (SWP) iq[slot] = ld_pin_u8(V.I0 + ipix0 + t * dipix);
         }
     };
 #pragma unroll
@@ -282,6 +304,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
 #pragma unroll
     for (int i = 0; i < KW; ++i) A[i] = INF2;   // no predecessor: L = C at the first pixel
     int prev_lo = -1;
+    int prev_i = 0;
     // steps to the next tile edge in x and in y (BLK)
     const int B = a.block_cut;
     int cx = 0x7FFFFFFF, cy = 0x7FFFFFFF;
@@ -315,6 +338,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                 }
             }
             const int cur_lo = (int)lq[u];
+            const int cur_i = (int)iq[u];
             issue(t + PF, u);
 
             // minimum of the predecessor over the path's lanes, in both halves
@@ -362,78 +386,178 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                 }
             }
 
-            // predecessor words around this lane's labels, HW halo words per side
-            uint32_t E[NE];
-#pragma unroll
-            for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
-#pragma unroll
-            for (int h = 0; h < HW; ++h) {
-                const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
-                const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
-                E[h] = gl == 0 ? INF2 : l;
-                E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
-            }
-            // a path whose window moved re-indexes its predecessor through shared memory
-            // (the whole warp does, when any of its paths moved)
+            // a path whose window moved re-indexes through shared memory (the whole warp
+            // does, when any of its paths moved)
             const int s = (WIN && act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
-            if (WIN && __any_sync(kFull, s != 0)) {
-                uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
+            uint32_t Mv[KW];   // the envelope M'(u) of this lane's labels
+            if constexpr (SWP) {
+                // this step's slopes: the table at the intensity step, at most T
+                const uint32_t P =
+                    (act && t > 0) ? min((uint32_t)slut[abs(cur_i - prev_i) & 0xFF], T) : P1;
+                const uint32_t Pu = P * up, Pd = P;
+                const uint32_t Cu1 = Pu * 0x10001u, Cd1 = Pd * 0x10001u;
+                uint32_t F[KW], Gd[KW];
+                // inside the lane: neighbours one label away, then whole words
 #pragma unroll
-                for (int i = 0; i < KW; ++i) gw[i] = A[i];
-                if (LAYER && asym) {
-                    uint32_t *sw = (uint32_t *)(sb + PAD + gl * K);
-#pragma unroll
-                    for (int i = 0; i < KW; ++i) sw[i] = SA[i];
-                    uint32_t *sl = (uint32_t *)(sb + PAD - DWP);
-                    for (int w = gl; w < DWP / 2; w += kG) sl[w] = m2;
+                for (int w = 0; w < KW; ++w) {
+                    // (absent, first label) and (last label, absent) at the lane's ends
+                    const uint32_t xl =
+                        w == 0 ? __byte_perm(A[0], INF2, 0x1054) : shift1(A[w - 1], A[w]);
+                    const uint32_t xr =
+                        w == KW - 1 ? __byte_perm(A[KW - 1], INF2, 0x7632) : shift1(A[w], A[w + 1]);
+                    F[w] = __viaddmin_u16x2(xl, Cu1, A[w]);
+                    Gd[w] = __viaddmin_u16x2(xr, Cd1, A[w]);
                 }
-                __syncwarp();
-                const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
-                const int j0 = PAD + gl * K - 2 * HW + sc;
-                const uint32_t *gwords = (const uint32_t *)gb + (j0 >> 1);
-                const uint32_t sel = (j0 & 1) ? 0x5432u : 0x3210u;
-                uint32_t Wd[NE + 1];
 #pragma unroll
-                for (int i = 0; i <= NE; ++i) Wd[i] = gwords[i];
+                for (int mw = 1; mw < KW; mw <<= 1) {
 #pragma unroll
-                for (int w = 0; w < NE; ++w) E[w] = __byte_perm(Wd[w], Wd[w + 1], sel);
-                if (LAYER && asym) {
-                    // current label j reads the predecessor's suffix minimum at j + s:
-                    // below its window every label is above (the minimum), beyond it none
+                    for (int w = KW - 1; w >= mw; --w)
+                        F[w] = __viaddmin_u16x2(F[w - mw], Cu1 * (2 * mw), F[w]);
+#pragma unroll
+                    for (int w = 0; w + mw < KW; ++w)
+                        Gd[w] = __viaddmin_u16x2(Gd[w + mw], Cd1 * (2 * mw), Gd[w]);
+                }
+                // across the lanes: F at the last label below this lane, G at the first label
+                // above it (scans of the lanes' end values, K labels per lane step)
+                int xf = __shfl_up_sync(kFull, (int)(F[KW - 1] >> 16), 1, kG);
+                int xg = __shfl_down_sync(kFull, (int)(Gd[0] & 0xFFFFu), 1, kG);
+                if (gl == 0) xf = (int)kInf16;
+                if (gl == kG - 1) xg = (int)kInf16;
+                const int su = (int)Pu * K, sd = (int)Pd * K;
+#pragma unroll
+                for (int o = 1; o < kG; o <<= 1) {
+                    const int vf = __shfl_up_sync(kFull, xf, o, kG);
+                    const int vg = __shfl_down_sync(kFull, xg, o, kG);
+                    if (gl >= o) xf = min(xf, vf + su * o);
+                    if (gl + o < kG) xg = min(xg, vg + sd * o);
+                }
+                const uint32_t xfp = (uint32_t)xf * 0x10001u, xgp = (uint32_t)xg * 0x10001u;
+#pragma unroll
+                for (int w = 0; w < KW; ++w) {
+                    // distances from the label below the lane (2w+1, 2w+2) and to the label
+                    // above it (K-2w, K-2w-1)
+                    const uint32_t du = (2u * w + 1) | ((2u * w + 2) << 16);
+                    const uint32_t dd = (uint32_t)(K - 2 * w) | ((uint32_t)(K - 2 * w - 1) << 16);
+                    F[w] = __viaddmin_u16x2(xfp, Pu * du, F[w]);
+                    Gd[w] = __viaddmin_u16x2(xgp, Pd * dd, Gd[w]);
+                    Mv[w] = __vminu2(__vminu2(F[w], Gd[w]), cap);
+                    if (asym) Mv[w] = __viaddmin_u16x2(SA[w], Tx2, Mv[w]);
+                }
+                if (WIN && __any_sync(kFull, s != 0)) {
+                    const int base = lane & ~(kG - 1);
+                    const int ftop = __shfl_sync(kFull, (int)(F[KW - 1] >> 16), base + kG - 1);
+                    const int gbot = __shfl_sync(kFull, (int)(Gd[0] & 0xFFFFu), base);
+                    uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
+#pragma unroll
+                    for (int i = 0; i < KW; ++i) gw[i] = Mv[i];
+                    __syncwarp();
                     const int s2 = min(max(s, -DWP), DWP);
                     const int j1 = PAD + gl * K + s2;
-                    const uint32_t *swords = (const uint32_t *)sb + (j1 >> 1);
-                    const uint32_t sel2 = (j1 & 1) ? 0x5432u : 0x3210u;
-                    uint32_t Sd[KW + 1];
+                    const uint32_t *mwords = (const uint32_t *)gb + (j1 >> 1);
+                    const uint32_t sel = (j1 & 1) ? 0x5432u : 0x3210u;
+                    uint32_t Wd[KW + 1];
 #pragma unroll
-                    for (int i = 0; i <= KW; ++i) Sd[i] = swords[i];
+                    for (int i = 0; i <= KW; ++i) Wd[i] = mwords[i];
 #pragma unroll
-                    for (int i = 0; i < KW; ++i) SA[i] = __byte_perm(Sd[i], Sd[i + 1], sel2);
+                    for (int i = 0; i < KW; ++i) Mv[i] = __byte_perm(Wd[i], Wd[i + 1], sel);
+                    __syncwarp();
+                    // labels outside the predecessor's window: F continued above its top
+                    // label, G below its first, each capped
+                    const int q0 = gl * K + s;
+                    if (q0 < 0 || q0 + K > DWP) {
+                        const int m2s = (int)(m2 & 0xFFFFu);
+                        const int capu = m2s + (int)(T * up), capd = m2s + (int)T;
+#pragma unroll
+                        for (int i = 0; i < KW; ++i) {
+                            uint32_t h2[2] = {Mv[i] & 0xFFFFu, Mv[i] >> 16};
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int q = q0 + 2 * i + h;
+                                if (q >= DWP)
+                                    h2[h] = (uint32_t)min(ftop + (int)Pu * (q - DWP + 1), capu);
+                                else if (q < 0)
+                                    h2[h] = (uint32_t)min(gbot + (int)Pd * (-q), capd);
+                            }
+                            Mv[i] = h2[0] | (h2[1] << 16);
+                        }
+                    }
                 }
-                __syncwarp();
-            }
-
-            uint32_t SH[NE - 1];
+            } else {
+                // predecessor words around this lane's labels, HW halo words per side
+                uint32_t E[NE];
 #pragma unroll
-            for (int j = 0; j < NE - 1; ++j) SH[j] = shift1(E[j], E[j + 1]);
+                for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
+#pragma unroll
+                for (int h = 0; h < HW; ++h) {
+                    const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
+                    const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
+                    E[h] = gl == 0 ? INF2 : l;
+                    E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
+                }
+                if (WIN && __any_sync(kFull, s != 0)) {
+                    uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
+#pragma unroll
+                    for (int i = 0; i < KW; ++i) gw[i] = A[i];
+                    if (LAYER && asym) {
+                        uint32_t *sw = (uint32_t *)(sb + PAD + gl * K);
+#pragma unroll
+                        for (int i = 0; i < KW; ++i) sw[i] = SA[i];
+                        uint32_t *sl = (uint32_t *)(sb + PAD - DWP);
+                        for (int w = gl; w < DWP / 2; w += kG) sl[w] = m2;
+                    }
+                    __syncwarp();
+                    const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
+                    const int j0 = PAD + gl * K - 2 * HW + sc;
+                    const uint32_t *gwords = (const uint32_t *)gb + (j0 >> 1);
+                    const uint32_t sel = (j0 & 1) ? 0x5432u : 0x3210u;
+                    uint32_t Wd[NE + 1];
+#pragma unroll
+                    for (int i = 0; i <= NE; ++i) Wd[i] = gwords[i];
+#pragma unroll
+                    for (int w = 0; w < NE; ++w) E[w] = __byte_perm(Wd[w], Wd[w + 1], sel);
+                    if (LAYER && asym) {
+                        // current label j reads the predecessor's suffix minimum at j + s:
+                        // below its window every label is above (the minimum), beyond it none
+                        const int s2 = min(max(s, -DWP), DWP);
+                        const int j1 = PAD + gl * K + s2;
+                        const uint32_t *swords = (const uint32_t *)sb + (j1 >> 1);
+                        const uint32_t sel2 = (j1 & 1) ? 0x5432u : 0x3210u;
+                        uint32_t Sd[KW + 1];
+#pragma unroll
+                        for (int i = 0; i <= KW; ++i) Sd[i] = swords[i];
+#pragma unroll
+                        for (int i = 0; i < KW; ++i) SA[i] = __byte_perm(Sd[i], Sd[i + 1], sel2);
+                    }
+                    __syncwarp();
+                }
+
+                uint32_t SH[NE - 1];
+#pragma unroll
+                for (int j = 0; j < NE - 1; ++j) SH[j] = shift1(E[j], E[j + 1]);
+
+#pragma unroll
+                for (int i = 0; i < KW; ++i) {
+                    const int e = HW + i;
+                    // words below e hold smaller labels: jumps up into (u, u+1)
+                    uint32_t m = __vminu2(E[e], cap);
+                    m = __viaddmin_u16x2(SH[e - 1], U1, m);
+                    m = __viaddmin_u16x2(SH[e], E1, m);
+                    m = __viaddmin_u16x2(E[e - 1], U2, m);
+                    m = __viaddmin_u16x2(E[e + 1], E2, m);
+                    if (RM >= 4) {
+                        m = __viaddmin_u16x2(SH[e - 2], U3, m);
+                        m = __viaddmin_u16x2(SH[e + 1], E3, m);
+                        m = __viaddmin_u16x2(E[e - 2], U4, m);
+                        m = __viaddmin_u16x2(E[e + 2], E4, m);
+                    }
+                    if (asym) m = __viaddmin_u16x2(SA[i], Tx2, m);
+                    Mv[i] = m;
+                }
+            }
 
 #pragma unroll
             for (int i = 0; i < KW; ++i) {
-                const int e = HW + i;
-                // words below e hold smaller labels: jumps up into (u, u+1)
-                uint32_t m = __vminu2(E[e], cap);
-                m = __viaddmin_u16x2(SH[e - 1], U1, m);
-                m = __viaddmin_u16x2(SH[e], E1, m);
-                m = __viaddmin_u16x2(E[e - 1], U2, m);
-                m = __viaddmin_u16x2(E[e + 1], E2, m);
-                if (RM >= 4) {
-                    m = __viaddmin_u16x2(SH[e - 2], U3, m);
-                    m = __viaddmin_u16x2(SH[e + 1], E3, m);
-                    m = __viaddmin_u16x2(E[e - 2], U4, m);
-                    m = __viaddmin_u16x2(E[e + 2], E4, m);
-                }
-                if (asym) m = __viaddmin_u16x2(SA[i], Tx2, m);
-                uint32_t L = c[i] + m - m2;      // per half: no carry, no borrow
+                uint32_t L = c[i] + Mv[i] - m2;      // per half: no carry, no borrow
                 if (padded) {
                     L &= keep[i];
                     A[i] = L | (INF2 & ~keep[i]);
@@ -455,6 +579,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                 }
             }
             prev_lo = cur_lo;
+            prev_i = cur_i;
         }
     }
     if (OUTN) {   // the last pixel of the longest paths: nothing follows to store it
@@ -470,14 +595,14 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     }
 }
 
-template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER = false>
+template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER = false, bool SWP = false>
 void launch_stencil(const LevelArgs &a, cudaStream_t s, const MergeArgs &mg = MergeArgs{},
                     int ndirs = 0)
 {
     const int maxp = a.W + a.H - 1;
     const int per_block = kStencilWarps * (32 / G);
     dim3 grid((maxp + per_block - 1) / per_block, ndirs ? ndirs : a.npaths, a.nviews);
-    agg_stencil<G, KW, RM, WIN, BLK, LAYER><<<grid, kStencilWarps * 32, 0, s>>>(a, mg);
+    agg_stencil<G, KW, RM, WIN, BLK, LAYER, SWP><<<grid, kStencilWarps * 32, 0, s>>>(a, mg);
 }
 
 // windows (pyramid levels below the top) and tiles (the top level only) never meet
@@ -494,6 +619,38 @@ void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
         if (win) launch_stencil<G, KW, 4, true, false>(a, s);
         else if (blk) launch_stencil<G, KW, 4, false, true>(a, s);
         else launch_stencil<G, KW, 4, false, false>(a, s);
+    }
+}
+
+// The gradient-weighted passes (a slope per step) as packed sweeps: 8 lanes per path for
+// strides of 16 and 32 labels, while the sweeps' largest value, the sentinel plus the
+// doubled slope (at most 2T) times the labels of a lane, stays below 2^16; a layer of the
+// layered merge also needs its energies far below the sentinel.
+bool sweep_ok(const LevelArgs &a, const MergeArgs &m)
+{
+    if (!m.lut || (a.Dws != 16 && a.Dws != 32)) return false;
+    const int64_t K = a.Dws / 8, up = m.double_up_dir >= 0 ? 2 : 1;
+    if ((int64_t)kInf16 + up * a.trunc * K >= 65536) return false;
+    return m.out_mode == 0 || 255 + 10 * (int64_t)a.trunc < (int64_t)kInf16;
+}
+
+template <int KW, bool LAYER>
+void launch_sweep_kw(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
+{
+    if (a.v[0].lo) launch_stencil<kLanesWide, KW, 2, true, false, LAYER, true>(a, s, m, m.ndirs);
+    else if (a.block_cut > 0)
+        launch_stencil<kLanesWide, KW, 2, false, true, LAYER, true>(a, s, m, m.ndirs);
+    else launch_stencil<kLanesWide, KW, 2, false, false, LAYER, true>(a, s, m, m.ndirs);
+}
+
+void launch_sweep(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
+{
+    if (m.out_mode == 1) {
+        if (a.Dws == 16) launch_sweep_kw<1, true>(a, m, s);
+        else launch_sweep_kw<2, true>(a, m, s);
+    } else {
+        if (a.Dws == 16) launch_sweep_kw<1, false>(a, m, s);
+        else launch_sweep_kw<2, false>(a, m, s);
     }
 }
 
@@ -1009,6 +1166,10 @@ void launch_scan8_k(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
 
 void launch_aggregate_general(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
 {
+    if (sweep_ok(a, m)) {
+        launch_sweep(a, m, s);
+        return;
+    }
     // 8 lanes per path for the strides of 16, 32 and 64 labels
     switch (a.Dws) {
     case 16: launch_scan8_k<2>(a, m, s); return;

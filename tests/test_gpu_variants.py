@@ -89,6 +89,11 @@ CASES = {
     "grad_zero_slopes": (lambda: synth.slanted_pair(128, 96, seed=48, d_max=40)[:2],
                          dict(max_disparity=48, num_scales=2, num_paths=8, p1=12, trunc=40),
                          np.where(np.arange(256) % 3 == 0, 0, 12).astype(np.int32)),
+    "grad_d128_s3_w32": (lambda: synth.slanted_pair(288, 160, seed=78, d_max=110)[:2],
+                         dict(max_disparity=128, num_scales=3, num_paths=8), exp_table(10, 16)),
+    "grad_tiles_s2_b16": (lambda: synth.slanted_pair(256, 160, seed=79, d_max=60)[:2],
+                          dict(max_disparity=64, num_scales=2, num_paths=8, top_block=16),
+                          exp_table(10, 8)),
     # both
     "paper_grad_s3": (lambda: synth.slanted_pair(224, 128, seed=49, d_max=56)[:2],
                       dict(max_disparity=64, num_scales=3, num_paths=8, merge_mode=PAPER),
