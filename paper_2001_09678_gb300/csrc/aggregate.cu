@@ -605,6 +605,16 @@ void launch_stencil(const LevelArgs &a, cudaStream_t s, const MergeArgs &mg = Me
     agg_stencil<G, KW, RM, WIN, BLK, LAYER, SWP><<<grid, kStencilWarps * 32, 0, s>>>(a, mg);
 }
 
+// Packed labels mark absent ones with the sentinel kInf16, which must exceed every cap
+// min_v A(v) + Tu that a step forms.  Without windows the predecessor's best label carries
+// over, so its minimum is at most a cost byte and the cap at most 255 + T.  With windows
+// that label can lie outside the current window: the minimum then reaches 255 + Tu and the
+// cap 255 + 2 Tu (Tu = T, or 2T for the doubled pass).  Beyond that the int32 kernels run.
+bool packed_caps_ok(const LevelArgs &a, int up)
+{
+    return !a.v[0].lo || 255 + 2 * up * (int64_t)a.trunc < (int64_t)kInf16;
+}
+
 // windows (pyramid levels below the top) and tiles (the top level only) never meet
 template <int G, int KW>
 void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
@@ -630,7 +640,7 @@ bool sweep_ok(const LevelArgs &a, const MergeArgs &m)
 {
     if (!m.lut || (a.Dws != 16 && a.Dws != 32)) return false;
     const int64_t K = a.Dws / 8, up = m.double_up_dir >= 0 ? 2 : 1;
-    if ((int64_t)kInf16 + up * a.trunc * K >= 65536) return false;
+    if ((int64_t)kInf16 + up * a.trunc * K >= 65536 || !packed_caps_ok(a, (int)up)) return false;
     return m.out_mode == 0 || 255 + 10 * (int64_t)a.trunc < (int64_t)kInf16;
 }
 
@@ -1237,7 +1247,7 @@ int launch_layer(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
 
 void launch_aggregate(const LevelArgs &a, cudaStream_t s)
 {
-    if (a.radius <= 4 && a.Dws <= 64) {
+    if (a.radius <= 4 && a.Dws <= 64 && packed_caps_ok(a, 1)) {
         const bool wide = a.lanes == kLanesWide;
         switch (a.Dws) {
         case 16:

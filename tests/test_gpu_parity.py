@@ -99,6 +99,17 @@ CASES = {
                 dict(max_disparity=192, num_scales=3, num_paths=8)),
     "dw64_s1": (lambda: synth.bands_pair(200, 60, seed=23, disparities=(10, 30, 55))[:2],
                 dict(max_disparity=64, num_scales=1, num_paths=8)),
+    # the largest range the boundary accepts
+    "max_range_d1024": (lambda: synth.bands_pair(1040, 24, seed=30,
+                                                 disparities=(100, 500, 900))[:2],
+                        dict(max_disparity=1024, num_scales=1, num_paths=4)),
+    # summed energies just below 2^16: paths * (255 + T) = 65528 and 65532
+    "energy_bound_8paths": (lambda: synth.slanted_pair(192, 96, seed=31, d_max=40)[:2],
+                            dict(max_disparity=48, num_scales=2, num_paths=8, p1=2000,
+                                 trunc=7936)),
+    "energy_bound_4paths": (lambda: synth.slanted_pair(192, 96, seed=32, d_max=40)[:2],
+                            dict(max_disparity=48, num_scales=2, num_paths=4, p1=4100,
+                                 trunc=16128)),
 }
 
 

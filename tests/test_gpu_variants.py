@@ -94,6 +94,16 @@ CASES = {
     "grad_tiles_s2_b16": (lambda: synth.slanted_pair(256, 160, seed=79, d_max=60)[:2],
                           dict(max_disparity=64, num_scales=2, num_paths=8, top_block=16),
                           exp_table(10, 8)),
+    "grad_energy_bound": (lambda: synth.slanted_pair(192, 96, seed=80, d_max=40)[:2],
+                          dict(max_disparity=48, num_scales=2, num_paths=8, p1=2000,
+                               trunc=7936), exp_table(2000, 16)),
+    # layered merge at its packed bound (255 + 10 T below the sentinel)
+    "paper_trunc_1612": (lambda: synth.slanted_pair(192, 96, seed=81, d_max=40)[:2],
+                         dict(max_disparity=48, num_scales=2, num_paths=8, p1=500, trunc=1612,
+                              merge_mode=PAPER), None),
+    "paper_grad_trunc_1612": (lambda: synth.slanted_pair(192, 96, seed=82, d_max=40)[:2],
+                              dict(max_disparity=48, num_scales=2, num_paths=8, p1=500,
+                                   trunc=1612, merge_mode=PAPER), exp_table(500, 16)),
     # both
     "paper_grad_s3": (lambda: synth.slanted_pair(224, 128, seed=49, d_max=56)[:2],
                       dict(max_disparity=64, num_scales=3, num_paths=8, merge_mode=PAPER),
