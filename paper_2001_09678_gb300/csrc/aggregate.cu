@@ -386,11 +386,92 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                 }
             }
 
-            // a path whose window moved re-indexes through shared memory (the whole warp
-            // does, when any of its paths moved)
-            const int s = (WIN && act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
-            uint32_t Mv[KW];   // the envelope M'(u) of this lane's labels
-            if constexpr (SWP) {
+            if constexpr (!SWP) {
+                // predecessor words around this lane's labels, HW halo words per side
+                uint32_t E[NE];
+#pragma unroll
+                for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
+#pragma unroll
+                for (int h = 0; h < HW; ++h) {
+                    const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
+                    const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
+                    E[h] = gl == 0 ? INF2 : l;
+                    E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
+                }
+                // a path whose window moved re-indexes its predecessor through shared memory
+                // (the whole warp does, when any of its paths moved)
+                const int s = (WIN && act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
+                if (WIN && __any_sync(kFull, s != 0)) {
+                    uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
+#pragma unroll
+                    for (int i = 0; i < KW; ++i) gw[i] = A[i];
+                    if (LAYER && asym) {
+                        uint32_t *sw = (uint32_t *)(sb + PAD + gl * K);
+#pragma unroll
+                        for (int i = 0; i < KW; ++i) sw[i] = SA[i];
+                        uint32_t *sl = (uint32_t *)(sb + PAD - DWP);
+                        for (int w = gl; w < DWP / 2; w += kG) sl[w] = m2;
+                    }
+                    __syncwarp();
+                    const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
+                    const int j0 = PAD + gl * K - 2 * HW + sc;
+                    const uint32_t *gwords = (const uint32_t *)gb + (j0 >> 1);
+                    const uint32_t sel = (j0 & 1) ? 0x5432u : 0x3210u;
+                    uint32_t Wd[NE + 1];
+#pragma unroll
+                    for (int i = 0; i <= NE; ++i) Wd[i] = gwords[i];
+#pragma unroll
+                    for (int w = 0; w < NE; ++w) E[w] = __byte_perm(Wd[w], Wd[w + 1], sel);
+                    if (LAYER && asym) {
+                        // current label j reads the predecessor's suffix minimum at j + s:
+                        // below its window every label is above (the minimum), beyond it none
+                        const int s2 = min(max(s, -DWP), DWP);
+                        const int j1 = PAD + gl * K + s2;
+                        const uint32_t *swords = (const uint32_t *)sb + (j1 >> 1);
+                        const uint32_t sel2 = (j1 & 1) ? 0x5432u : 0x3210u;
+                        uint32_t Sd[KW + 1];
+#pragma unroll
+                        for (int i = 0; i <= KW; ++i) Sd[i] = swords[i];
+#pragma unroll
+                        for (int i = 0; i < KW; ++i) SA[i] = __byte_perm(Sd[i], Sd[i + 1], sel2);
+                    }
+                    __syncwarp();
+                }
+
+                uint32_t SH[NE - 1];
+#pragma unroll
+                for (int j = 0; j < NE - 1; ++j) SH[j] = shift1(E[j], E[j + 1]);
+
+#pragma unroll
+                for (int i = 0; i < KW; ++i) {
+                    const int e = HW + i;
+                    // words below e hold smaller labels: jumps up into (u, u+1)
+                    uint32_t m = __vminu2(E[e], cap);
+                    m = __viaddmin_u16x2(SH[e - 1], U1, m);
+                    m = __viaddmin_u16x2(SH[e], E1, m);
+                    m = __viaddmin_u16x2(E[e - 1], U2, m);
+                    m = __viaddmin_u16x2(E[e + 1], E2, m);
+                    if (RM >= 4) {
+                        m = __viaddmin_u16x2(SH[e - 2], U3, m);
+                        m = __viaddmin_u16x2(SH[e + 1], E3, m);
+                        m = __viaddmin_u16x2(E[e - 2], U4, m);
+                        m = __viaddmin_u16x2(E[e + 2], E4, m);
+                    }
+                    if (asym) m = __viaddmin_u16x2(SA[i], Tx2, m);
+                    uint32_t L = c[i] + m - m2;      // per half: no carry, no borrow
+                    if (padded) {
+                        L &= keep[i];
+                        A[i] = L | (INF2 & ~keep[i]);
+                    } else {
+                        A[i] = L;
+                    }
+                    c[i] = L;
+                }
+            } else {
+                // a path whose window moved re-indexes its envelope through shared memory
+                // (the whole warp does, when any of its paths moved)
+                const int s = (WIN && act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
+                uint32_t Mv[KW];   // the envelope M'(u) of this lane's labels
                 // this step's slopes: the table at the intensity step, at most T
                 const uint32_t P =
                     (act && t > 0) ? min((uint32_t)slut[abs(cur_i - prev_i) & 0xFF], T) : P1;
@@ -482,89 +563,17 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                         }
                     }
                 }
-            } else {
-                // predecessor words around this lane's labels, HW halo words per side
-                uint32_t E[NE];
-#pragma unroll
-                for (int i = 0; i < KW; ++i) E[HW + i] = A[i];
-#pragma unroll
-                for (int h = 0; h < HW; ++h) {
-                    const uint32_t l = __shfl_up_sync(kFull, A[KW - HW + h], 1, kG);
-                    const uint32_t r = __shfl_down_sync(kFull, A[h], 1, kG);
-                    E[h] = gl == 0 ? INF2 : l;
-                    E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
-                }
-                if (WIN && __any_sync(kFull, s != 0)) {
-                    uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
-#pragma unroll
-                    for (int i = 0; i < KW; ++i) gw[i] = A[i];
-                    if (LAYER && asym) {
-                        uint32_t *sw = (uint32_t *)(sb + PAD + gl * K);
-#pragma unroll
-                        for (int i = 0; i < KW; ++i) sw[i] = SA[i];
-                        uint32_t *sl = (uint32_t *)(sb + PAD - DWP);
-                        for (int w = gl; w < DWP / 2; w += kG) sl[w] = m2;
-                    }
-                    __syncwarp();
-                    const int sc = min(max(s, -(DWP + 2 * HW)), DWP + 2 * HW);
-                    const int j0 = PAD + gl * K - 2 * HW + sc;
-                    const uint32_t *gwords = (const uint32_t *)gb + (j0 >> 1);
-                    const uint32_t sel = (j0 & 1) ? 0x5432u : 0x3210u;
-                    uint32_t Wd[NE + 1];
-#pragma unroll
-                    for (int i = 0; i <= NE; ++i) Wd[i] = gwords[i];
-#pragma unroll
-                    for (int w = 0; w < NE; ++w) E[w] = __byte_perm(Wd[w], Wd[w + 1], sel);
-                    if (LAYER && asym) {
-                        // current label j reads the predecessor's suffix minimum at j + s:
-                        // below its window every label is above (the minimum), beyond it none
-                        const int s2 = min(max(s, -DWP), DWP);
-                        const int j1 = PAD + gl * K + s2;
-                        const uint32_t *swords = (const uint32_t *)sb + (j1 >> 1);
-                        const uint32_t sel2 = (j1 & 1) ? 0x5432u : 0x3210u;
-                        uint32_t Sd[KW + 1];
-#pragma unroll
-                        for (int i = 0; i <= KW; ++i) Sd[i] = swords[i];
-#pragma unroll
-                        for (int i = 0; i < KW; ++i) SA[i] = __byte_perm(Sd[i], Sd[i + 1], sel2);
-                    }
-                    __syncwarp();
-                }
-
-                uint32_t SH[NE - 1];
-#pragma unroll
-                for (int j = 0; j < NE - 1; ++j) SH[j] = shift1(E[j], E[j + 1]);
-
 #pragma unroll
                 for (int i = 0; i < KW; ++i) {
-                    const int e = HW + i;
-                    // words below e hold smaller labels: jumps up into (u, u+1)
-                    uint32_t m = __vminu2(E[e], cap);
-                    m = __viaddmin_u16x2(SH[e - 1], U1, m);
-                    m = __viaddmin_u16x2(SH[e], E1, m);
-                    m = __viaddmin_u16x2(E[e - 1], U2, m);
-                    m = __viaddmin_u16x2(E[e + 1], E2, m);
-                    if (RM >= 4) {
-                        m = __viaddmin_u16x2(SH[e - 2], U3, m);
-                        m = __viaddmin_u16x2(SH[e + 1], E3, m);
-                        m = __viaddmin_u16x2(E[e - 2], U4, m);
-                        m = __viaddmin_u16x2(E[e + 2], E4, m);
+                    uint32_t L = c[i] + Mv[i] - m2;      // per half: no carry, no borrow
+                    if (padded) {
+                        L &= keep[i];
+                        A[i] = L | (INF2 & ~keep[i]);
+                    } else {
+                        A[i] = L;
                     }
-                    if (asym) m = __viaddmin_u16x2(SA[i], Tx2, m);
-                    Mv[i] = m;
+                    c[i] = L;
                 }
-            }
-
-#pragma unroll
-            for (int i = 0; i < KW; ++i) {
-                uint32_t L = c[i] + Mv[i] - m2;      // per half: no carry, no borrow
-                if (padded) {
-                    L &= keep[i];
-                    A[i] = L | (INF2 & ~keep[i]);
-                } else {
-                    A[i] = L;
-                }
-                c[i] = L;
             }
             if (act && !OUTN) {
                 if (KW % 2 == 0) {
