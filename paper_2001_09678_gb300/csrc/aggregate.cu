@@ -176,7 +176,10 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     constexpr int DWP = kG * K;              // labels per path (= the volume stride)
     constexpr int PAD = (DWP + 4 * HW + 2 + 7) / 8 * 8;  // absent labels around a path
     constexpr int BUF = 2 * PAD + DWP;
-    constexpr int PF = KW <= 4 ? 8 : 4;      // prefetch distance (steps)
+    // prefetch distance (steps), measured: 12 for the summed pass with two words per lane
+    // (8 lanes on 32 labels), 8 for the other shapes and for the layer and sweep modes
+    // (each slower at 12), 4 for the widest lanes
+    constexpr int PF = KW > 4 ? 4 : (KW == 2 && !LAYER && !SWP ? 12 : 8);
     constexpr int CW = KW >= 2 ? KW / 2 : 1; // 32-bit words of cost bytes per lane
 
     __shared__ __align__(16) uint16_t rbuf[WIN ? kStencilWarps * kPathsPerWarp * BUF : 8];
@@ -341,6 +344,12 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
             const int cur_i = (int)iq[u];
             issue(t + PF, u);
 
+            // this step's window shift, known from the prefetched window starts: a path whose
+            // window moved re-indexes through shared memory (the whole warp does, when any of
+            // its paths moved); voted here, ahead of the shuffles that depend on A
+            const int s = (WIN && act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
+            const bool moved = WIN && __any_sync(kFull, s != 0);
+
             // minimum of the predecessor over the path's lanes, in both halves
             uint32_t m2 = A[0];
 #pragma unroll
@@ -398,10 +407,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                     E[h] = gl == 0 ? INF2 : l;
                     E[HW + KW + h] = gl == kG - 1 ? INF2 : r;
                 }
-                // a path whose window moved re-indexes its predecessor through shared memory
-                // (the whole warp does, when any of its paths moved)
-                const int s = (WIN && act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
-                if (WIN && __any_sync(kFull, s != 0)) {
+                if (moved) {   // re-index the predecessor
                     uint32_t *gw = (uint32_t *)(gb + PAD + gl * K);
 #pragma unroll
                     for (int i = 0; i < KW; ++i) gw[i] = A[i];
@@ -468,9 +474,6 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                     c[i] = L;
                 }
             } else {
-                // a path whose window moved re-indexes its envelope through shared memory
-                // (the whole warp does, when any of its paths moved)
-                const int s = (WIN && act && prev_lo >= 0) ? cur_lo - prev_lo : 0;
                 uint32_t Mv[KW];   // the envelope M'(u) of this lane's labels
                 // this step's slopes: the table at the intensity step, at most T
                 const uint32_t P =
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
                     Mv[w] = __vminu2(__vminu2(F[w], Gd[w]), cap);
                     if (asym) Mv[w] = __viaddmin_u16x2(SA[w], Tx2, Mv[w]);
                 }
-                if (WIN && __any_sync(kFull, s != 0)) {
+                if (moved) {   // re-index the envelope
                     const int base = lane & ~(kG - 1);
                     const int ftop = __shfl_sync(kFull, (int)(F[KW - 1] >> 16), base + kG - 1);
                     const int gbot = __shfl_sync(kFull, (int)(Gd[0] & 0xFFFFu), base);
