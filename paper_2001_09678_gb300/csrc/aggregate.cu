@@ -165,7 +165,9 @@ __device__ __forceinline__ void store_normalised(uint16_t *dst, const uint32_t (
 // labels of a lane, which the dispatch keeps below 2^16.  With windows, the envelope is
 // formed in the predecessor's frame and re-indexed; labels beyond the predecessor's window
 // continue the sweeps linearly from its edge, capped.
-template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER, bool SWP>
+// XM: the path minimum through shared memory instead of shuffles (8-lane paths; chosen at
+// dispatch where measured faster).
+template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER, bool SWP, bool XM>
 __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, MergeArgs mg)
 {
     constexpr int kG = G;                    // lanes per scan path
@@ -181,12 +183,14 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     // (each slower at 12), 4 for the widest lanes
     constexpr int PF = KW > 4 ? 4 : (KW == 2 && !LAYER && !SWP ? 12 : 8);
     constexpr int CW = KW >= 2 ? KW / 2 : 1; // 32-bit words of cost bytes per lane
+    static_assert(kG == 4 || kG == 8, "paths of 4 or 8 lanes");
 
     __shared__ __align__(16) uint16_t rbuf[WIN ? kStencilWarps * kPathsPerWarp * BUF : 8];
     // suffix minima of the predecessor for the doubled pass: lower pad = the path's
     // minimum (every predecessor label lies above), upper pad absent
     __shared__ __align__(16) uint16_t sbuf[WIN && LAYER && !SWP ? kStencilWarps * kPathsPerWarp * BUF : 8];
     __shared__ int slut[SWP ? 256 : 1];      // the gradient table's slopes
+    __shared__ __align__(16) uint32_t redbuf[2 * kStencilWarps * 32];   // path minima
     if (SWP) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) slut[i] = mg.lut[i];
         __syncthreads();
@@ -356,8 +360,23 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
             for (int i = 1; i < KW; ++i) m2 = __vminu2(m2, A[i]);
             m2 = __vminu2(m2, __byte_perm(m2, m2, 0x1032));
             uint32_t lm = m2;                 // this lane's minimum
+            if constexpr (!XM || kG != 8) {
 #pragma unroll
-            for (int o = 1; o < kG; o <<= 1) m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, o));
+                for (int o = 1; o < kG; o <<= 1) m2 = __vminu2(m2, __shfl_xor_sync(kFull, m2, o));
+            } else {
+                // the 8 lane minima of the path through shared memory (one store, one warp
+                // barrier, two 16-byte loads) instead of three dependent shuffles: the
+                // exchange is on every step's dependent chain.  Double-buffered by step
+                // parity, so a lane's next store never meets a read of this step.
+                uint32_t *rw = redbuf + ((t & 1) * kStencilWarps + warp) * 32;
+                rw[lane] = lm;
+                __syncwarp();
+                const uint4 *g4 = (const uint4 *)(rw + grp * kG);
+                const uint4 q0 = g4[0];
+                const uint32_t r = __vminu2(__vminu2(q0.x, q0.y), __vminu2(q0.z, q0.w));
+                const uint4 q1 = g4[1];
+                m2 = __vminu2(r, __vminu2(__vminu2(q1.x, q1.y), __vminu2(q1.z, q1.w)));
+            }
             if (OUTN && t > 0 && t - 1 < n)   // the previous pixel, normalised by its minimum
                 store_normalised<KW>(outv + (int64_t)(pix - dpix) * DWP + gl * K, A, m2, keep,
                                      padded);
@@ -607,14 +626,15 @@ __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, M
     }
 }
 
-template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER = false, bool SWP = false>
+template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER = false, bool SWP = false,
+          bool XM = false>
 void launch_stencil(const LevelArgs &a, cudaStream_t s, const MergeArgs &mg = MergeArgs{},
                     int ndirs = 0)
 {
     const int maxp = a.W + a.H - 1;
     const int per_block = kStencilWarps * (32 / G);
     dim3 grid((maxp + per_block - 1) / per_block, ndirs ? ndirs : a.npaths, a.nviews);
-    agg_stencil<G, KW, RM, WIN, BLK, LAYER, SWP><<<grid, kStencilWarps * 32, 0, s>>>(a, mg);
+    agg_stencil<G, KW, RM, WIN, BLK, LAYER, SWP, XM><<<grid, kStencilWarps * 32, 0, s>>>(a, mg);
 }
 
 // Packed labels mark absent ones with the sentinel kInf16, which must exceed every cap
@@ -633,6 +653,16 @@ void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
 {
     const bool win = a.v[0].lo != nullptr;
     const bool blk = a.block_cut > 0;
+    // the shared-memory path minimum: measured faster on 8 lanes of two words without
+    // padding labels, slower with one word per lane or with padding
+    if constexpr (G == 8 && KW == 2) {
+        if (a.Dw == a.Dws && a.radius <= 2) {
+            if (win) launch_stencil<G, KW, 2, true, false, false, false, true>(a, s);
+            else if (blk) launch_stencil<G, KW, 2, false, true, false, false, true>(a, s);
+            else launch_stencil<G, KW, 2, false, false, false, false, true>(a, s);
+            return;
+        }
+    }
     if (a.radius <= 2) {
         if (win) launch_stencil<G, KW, 2, true, false>(a, s);
         else if (blk) launch_stencil<G, KW, 2, false, true>(a, s);
@@ -659,10 +689,12 @@ bool sweep_ok(const LevelArgs &a, const MergeArgs &m)
 template <int KW, bool LAYER>
 void launch_sweep_kw(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
 {
-    if (a.v[0].lo) launch_stencil<kLanesWide, KW, 2, true, false, LAYER, true>(a, s, m, m.ndirs);
+    // (the shared-memory path minimum measured faster in the layer mode only)
+    if (a.v[0].lo)
+        launch_stencil<kLanesWide, KW, 2, true, false, LAYER, true, LAYER>(a, s, m, m.ndirs);
     else if (a.block_cut > 0)
-        launch_stencil<kLanesWide, KW, 2, false, true, LAYER, true>(a, s, m, m.ndirs);
-    else launch_stencil<kLanesWide, KW, 2, false, false, LAYER, true>(a, s, m, m.ndirs);
+        launch_stencil<kLanesWide, KW, 2, false, true, LAYER, true, LAYER>(a, s, m, m.ndirs);
+    else launch_stencil<kLanesWide, KW, 2, false, false, LAYER, true, LAYER>(a, s, m, m.ndirs);
 }
 
 void launch_sweep(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
@@ -1228,13 +1260,13 @@ void launch_layer_kw(const LevelArgs &a, const MergeArgs &m, cudaStream_t s)
     const bool win = a.v[0].lo != nullptr;
     const bool blk = a.block_cut > 0;
     if (a.radius <= 2) {
-        if (win) launch_stencil<G, KW, 2, true, false, true>(a, s, m, m.ndirs);
-        else if (blk) launch_stencil<G, KW, 2, false, true, true>(a, s, m, m.ndirs);
-        else launch_stencil<G, KW, 2, false, false, true>(a, s, m, m.ndirs);
+        if (win) launch_stencil<G, KW, 2, true, false, true, false, G == 8>(a, s, m, m.ndirs);
+        else if (blk) launch_stencil<G, KW, 2, false, true, true, false, G == 8>(a, s, m, m.ndirs);
+        else launch_stencil<G, KW, 2, false, false, true, false, G == 8>(a, s, m, m.ndirs);
     } else if constexpr (KW >= 2) {
-        if (win) launch_stencil<G, KW, 4, true, false, true>(a, s, m, m.ndirs);
-        else if (blk) launch_stencil<G, KW, 4, false, true, true>(a, s, m, m.ndirs);
-        else launch_stencil<G, KW, 4, false, false, true>(a, s, m, m.ndirs);
+        if (win) launch_stencil<G, KW, 4, true, false, true, false, G == 8>(a, s, m, m.ndirs);
+        else if (blk) launch_stencil<G, KW, 4, false, true, true, false, G == 8>(a, s, m, m.ndirs);
+        else launch_stencil<G, KW, 4, false, false, true, false, G == 8>(a, s, m, m.ndirs);
     }
 }
 
