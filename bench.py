@@ -216,10 +216,21 @@ def replica_throughput(units_per_step, steps, world, slowest_ms):
     return world * steps * units_per_step / (slowest_ms / 1e3) / 1e6
 
 
+def code_hash(path):
+    """sha256 prefix of a C/CUDA source with its comments, trailing blanks and empty lines
+    removed: edits to comments leave it unchanged, edits to code do not."""
+    import hashlib
+    import re
+    text = open(path, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    code = "\n".join(ln for ln in lines if ln)
+    return hashlib.sha256(code.encode("utf-8")).hexdigest()[:16]
+
+
 def measured_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
-    kernel's source changed since the capture."""
-    import hashlib
+    kernel's code changed since the capture."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -230,8 +241,7 @@ def measured_traffic(kernel):
         src = os.path.join(ROOT, kv["source"])
         if not os.path.exists(src):
             return None
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return int(kv["bytes_per_launch"]) if h == kv["sha256_16"] else None
+        return int(kv["bytes_per_launch"]) if code_hash(src) == kv["code_sha256_16"] else None
     return None
 
 

@@ -9,24 +9,28 @@
 // are virtual nodes (absent).  Energies are kept in the bounded form
 //     L(p,u) = C(p,u) + M'(u) - min_v L(p-r,v),   M'(u) = min_v L(p-r,v) + eps(u,v),
 // a per-pixel constant shift of the literal recursion that leaves every argmin unchanged
-// and keeps every value below 8192; each pass adds L into the summed volume S.
+// and keeps every value small (at most 255 + T per pass); each pass adds L into the summed
+// volume S, or, in the paper's layered merge, stores it min-normalised for the next layer.
 //
-// Two kernels:
-//  * agg_stencil: when the truncation makes every jump of more than R labels cost T
-//    (R = ceil(T/p1) - 1 <= 4; the default p1 = 10, T = 30 gives R = 2), the two sweeps
-//    reduce to  M'(u) = min(min_{|d|<=R} L(p-r,u+d) + p1|d|, min_v L(p-r,v) + T).
-//    Four lanes own one scan path, each lane 2*KW consecutive labels packed two per
-//    32-bit register; the stencil is packed 16-bit add-min arithmetic, the halo words
-//    come from the neighbouring lanes by shuffles, and a window shift between
-//    consecutive pixels (pyramid levels) re-indexes the predecessor through shared
-//    memory.  S is accumulated with 64-bit reductions of four packed labels.  In its
-//    layer mode it runs one layer of the paper's layered merge (Section 3.2), the
-//    left-to-right pass with doubled upward jumps included.
-//  * agg_general: any R and window width: one warp per scan path, the two sweeps written
-//    as prefix minima  min_{v<=u} A(v) + p1 (u-v) = p1 u + min_{v<=u} (A(v) - p1 v)
-//    (and the mirror image), evaluated by shuffle scans over the lanes.  It also runs
-//    the variants the stencil cannot: a slope per step from the image gradient (Eq. EU),
-//    and the layered merge at radii or widths outside the stencil's.
+// Three kernels:
+//  * agg_stencil: 4 or 8 lanes own one scan path, each lane 2*KW consecutive labels packed
+//    two per 32-bit register (16-bit energies, absent labels = the sentinel 16384).  When
+//    the truncation makes every jump of more than R labels cost T (R = ceil(T/p1) - 1 <= 4;
+//    the default p1 = 10, T = 30 gives R = 2), the two sweeps reduce to
+//        M'(u) = min(min_{|d|<=R} L(p-r,u+d) + min(p1|d|, T), min_v L(p-r,v) + T),
+//    packed add-min arithmetic over halo words from the neighbouring lanes.  The path's
+//    minimum is exchanged through shared memory or by shuffles, a window shift between
+//    consecutive pixels (pyramid levels) re-indexes the predecessor through shared memory,
+//    and S is accumulated with 64-bit reductions of four packed labels.  Its layer mode
+//    runs one layer of the layered merge (Section 3.2), the left-to-right pass with doubled
+//    upward jumps included; its sweep mode runs gradient-weighted slopes (Eq. EU) as
+//    untruncated packed sweeps.
+//  * agg_scan8: 8 lanes per path, int32 labels, the two sweeps as segmented prefix and
+//    suffix minima across the lanes: the gradient and layered variants outside the packed
+//    kernel's bounds or widths.
+//  * agg_general: any window width: one warp per scan path, the sweeps written as prefix
+//    minima  min_{v<=u} A(v) + p1 (u-v) = p1 u + min_{v<=u} (A(v) - p1 v)  (and the mirror
+//    image), evaluated by shuffle scans over the lanes.
 #include "mpv_internal.cuh"
 
 namespace mpv {

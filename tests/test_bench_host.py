@@ -28,18 +28,20 @@ def test_algorithmic_bytes():
     assert lay["wta"] - alg["wta"] == 2 * 2 * nodes   # the last pair is read, not one S
 
 
-def test_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeypatch):
-    import hashlib
+def test_traffic_is_reported_only_for_the_captured_code(tmp_path, monkeypatch):
     import os
     src = tmp_path / "k.cu"
-    src.write_text("kernel v1")
-    h = hashlib.sha256(b"kernel v1").hexdigest()[:16]
+    src.write_text("// what it does\nint k() { return 1; }  // one\n")
+    h = bench.code_hash(str(src))
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "k_traffic.txt").write_text(
-        f"# comment\nkernel=k source=k.cu sha256_16={h} bytes_per_launch=1234\n")
+        f"# comment\nkernel=k source=k.cu code_sha256_16={h} bytes_per_launch=1234\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_traffic("k") == 1234
-    src.write_text("kernel v2")                        # the kernel changed: no traffic
+    # comments and blank lines edited: the same code, the same traffic
+    src.write_text("/* what\n   it does */\n\nint k() { return 1; }\n// the end\n")
+    assert bench.measured_traffic("k") == 1234
+    src.write_text("int k() { return 2; }\n")         # the code changed: no traffic
     assert bench.measured_traffic("k") is None
     assert bench.measured_traffic("absent") is None
     assert os.path.exists(tmp_path / "profiles" / "k_traffic.txt")
