@@ -75,6 +75,19 @@ struct ImageJob {       // one 2x2 down-sampling or mirror job
 
 void launch_mirror(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s);
 void launch_down2(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s);
+
+struct PyrJob {         // the next two pyramid levels of one image (pyramid2_kernel)
+    const uint8_t *src;  // source level, W x H
+    int src_pitch;
+    int mirror;          // read the source mirrored (x -> W-1-x)
+    uint8_t *full;       // optional: the mirrored source written out
+    int full_pitch;
+    uint8_t *d1;         // the level below the source
+    int p1;
+    uint8_t *d2;         // optional: the level below that
+    int p2;
+};
+void launch_pyramid2(const PyrJob *jobs, int njobs, int W, int H, cudaStream_t s);
 void launch_seed(const SeedArgs &a, cudaStream_t s);
 void launch_cost(const LevelArgs &a, cudaStream_t s);
 void launch_aggregate(const LevelArgs &a, cudaStream_t s);

@@ -209,14 +209,38 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
     I1[0][top] = job.right;
     P0[0][top] = P1[0][top] = job.pitch;
 
-    // right view: the mirrored, swapped pair
-    if (nviews == 2) {
+    // right view: the mirrored, swapped pair.  The first two levels below the input come
+    // from one launch that also writes the mirrored inputs; further levels one by one.
+    if (top == 0 && nviews == 2) {
         HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
         ImageJob m[2] = {{job.right, job.pitch, base + L.img0[1][top], g.pitch[top]},
                          {job.left, job.pitch, base + L.img1[1][top], g.pitch[top]}};
         launch_mirror(m, 2, job.W, job.H, s);
     }
-    for (int l = top - 1; l >= 0; --l) {
+    if (top >= 1) {
+        HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
+        const int l1 = top - 1, l2 = top - 2;
+        PyrJob pj[4];
+        int n = 0;
+        for (int v = 0; v < nviews; ++v)
+            for (int k = 0; k < 2; ++k) {
+                // view 0: (left, right); view 1: (mirrored right, mirrored left)
+                const uint8_t *src = (v == 0) == (k == 0) ? job.left : job.right;
+                const size_t *dimg = k == 0 ? L.img0[v] : L.img1[v];
+                PyrJob &j = pj[n++];
+                j.src = src;
+                j.src_pitch = job.pitch;
+                j.mirror = v;
+                j.full = v ? base + dimg[top] : nullptr;
+                j.full_pitch = g.pitch[top];
+                j.d1 = base + dimg[l1];
+                j.p1 = g.pitch[l1];
+                j.d2 = l2 >= 0 ? base + dimg[l2] : nullptr;
+                j.p2 = l2 >= 0 ? g.pitch[l2] : 0;
+            }
+        launch_pyramid2(pj, n, job.W, job.H, s);
+    }
+    for (int l = top - 3; l >= 0; --l) {
         HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
         ImageJob jobs[4];
         int n = 0;

@@ -24,6 +24,10 @@ struct Jobs4 {
     ImageJob j[4];
 };
 
+struct PyrJobs4 {
+    PyrJob j[4];
+};
+
 // 2x2 box mean, round half up; the last row/column is replicated when odd.
 __global__ void down2_kernel(Jobs4 jobs, int W, int H)
 {
@@ -38,6 +42,58 @@ __global__ void down2_kernel(Jobs4 jobs, int W, int H)
     const uint8_t *r1 = j.src + (int64_t)y1 * j.src_pitch;
     const int s = r0[x0] + r0[x1] + r1[x0] + r1[x1];
     j.dst[(int64_t)y * j.dst_pitch + x] = (uint8_t)((s + 2) >> 2);
+}
+
+// The next two pyramid levels of up to four images in one launch, the first from the
+// source (read mirrored for the right view's pair, whose full-resolution copy is written
+// on the way), the second from the first through shared memory.  Same arithmetic as two
+// down2_kernel passes: 2x2 box mean, round half up, last row/column replicated when odd
+// at each level.  A block makes 64 x 2 pixels of the first level and 32 x 1 of the second.
+constexpr int kPyrCols = 64;
+
+__global__ void __launch_bounds__(2 * kPyrCols) pyramid2_kernel(PyrJobs4 jobs, int W, int H)
+{
+    const PyrJob j = jobs.j[blockIdx.z];
+    const int W1 = (W + 1) >> 1, H1 = (H + 1) >> 1;
+    const int tx = threadIdx.x % kPyrCols, ty = threadIdx.x / kPyrCols;
+    const int x = blockIdx.x * kPyrCols + tx, y = blockIdx.y * 2 + ty;
+    __shared__ uint8_t t1[2][kPyrCols];
+    if (x < W1 && y < H1) {
+        const int x0 = 2 * x, x1 = min(2 * x + 1, W - 1);
+        const int y0 = 2 * y, y1 = min(2 * y + 1, H - 1);
+        const int c0 = j.mirror ? W - 1 - x0 : x0, c1 = j.mirror ? W - 1 - x1 : x1;
+        const uint8_t *r0 = j.src + (int64_t)y0 * j.src_pitch;
+        const uint8_t *r1 = j.src + (int64_t)y1 * j.src_pitch;
+        const int a = r0[c0], b = r0[c1], c = r1[c0], d = r1[c1];
+        const uint8_t v = (uint8_t)((a + b + c + d + 2) >> 2);
+        j.d1[(int64_t)y * j.p1 + x] = v;
+        t1[ty][tx] = v;
+        if (j.full) {   // each full-resolution pixel of the mirrored copy once
+            uint8_t *f0 = j.full + (int64_t)y0 * j.full_pitch;
+            f0[x0] = (uint8_t)a;
+            if (2 * x + 1 < W) f0[x0 + 1] = (uint8_t)b;
+            if (2 * y + 1 < H) {
+                uint8_t *f1 = f0 + j.full_pitch;
+                f1[x0] = (uint8_t)c;
+                if (2 * x + 1 < W) f1[x0 + 1] = (uint8_t)d;
+            }
+        }
+    }
+    if (!j.d2) return;   // the same for the whole block (one image per blockIdx.z)
+    __syncthreads();
+    if (threadIdx.x < kPyrCols / 2) {
+        const int W2 = (W1 + 1) >> 1, H2 = (H1 + 1) >> 1;
+        const int X = blockIdx.x * (kPyrCols / 2) + threadIdx.x, Y = blockIdx.y;
+        if (X < W2 && Y < H2) {
+            // first-level pixels 2X, min(2X+1, W1-1) and rows 2Y, min(2Y+1, H1-1): all in
+            // this block's tile
+            const int u0 = 2 * threadIdx.x;
+            const int u1 = min(2 * X + 1, W1 - 1) - blockIdx.x * kPyrCols;
+            const int v1 = min(2 * Y + 1, H1 - 1) - 2 * Y;
+            const int sum = t1[0][u0] + t1[0][u1] + t1[v1][u0] + t1[v1][u1];
+            j.d2[(int64_t)Y * j.p2 + X] = (uint8_t)((sum + 2) >> 2);
+        }
+    }
 }
 
 __global__ void seed_kernel(SeedArgs a)
@@ -230,6 +286,15 @@ void launch_down2(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s)
     const int W2 = (W + 1) / 2, H2 = (H + 1) / 2;
     dim3 grid((W2 + 127) / 128, H2, njobs);
     down2_kernel<<<grid, 128, 0, s>>>(j4, W, H);
+}
+
+void launch_pyramid2(const PyrJob *jobs, int njobs, int W, int H, cudaStream_t s)
+{
+    PyrJobs4 j4;
+    for (int i = 0; i < 4; ++i) j4.j[i] = jobs[i < njobs ? i : 0];
+    const int W1 = (W + 1) / 2, H1 = (H + 1) / 2;
+    dim3 grid((W1 + kPyrCols - 1) / kPyrCols, (H1 + 1) / 2, njobs);
+    pyramid2_kernel<<<grid, 2 * kPyrCols, 0, s>>>(j4, W, H);
 }
 
 void launch_seed(const SeedArgs &a, cudaStream_t s)
