@@ -150,6 +150,11 @@ __global__ void __launch_bounds__(kCostThreads) cost_kernel(LevelArgs a, int usp
     int4 *st0 = (int4 *)(smem + L.off_st0);
     int4 *st1 = (int4 *)(smem + L.off_st1);
 
+    if (a.zero_s) {   // this segment's summed energies start at zero (16-byte stores)
+        uint4 *sz = (uint4 *)(V.S + ((int64_t)y * W + x0) * Dws);
+        const int n16 = npx * Dws / 8;     // Dws is a multiple of 16
+        for (int i = tid; i < n16; i += kCostThreads) sz[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (tid == 0) {
         red[0] = 0x7FFFFFFF;
         red[1] = 0;

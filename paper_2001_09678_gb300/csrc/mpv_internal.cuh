@@ -51,6 +51,7 @@ struct LevelArgs {
     int lanes;       // lanes per scan path for 32/64-label strides (4 or 8; autotuned)
     unsigned long long *edge;  // optional [2]: WTA at a window edge inside the range, pixels
     int block_cut;   // > 0: independent block_cut x block_cut tiles (scan paths restart)
+    int zero_s;      // the cost kernel also clears S (the summed merge accumulates into it)
 };
 
 // Launch shapes chosen per image shape by the autotuner.

@@ -315,6 +315,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
         }
         {
             HookScope hs(hook, MPV_STAGE_COST, 1, s);
+            a.zero_s = !layered;   // the summed merge: instead of a memset of S
             launch_cost(a, s);
         }
         if (learned && l == 0) {
@@ -380,9 +381,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             }
         } else {
             HookScope hs(hook, MPV_STAGE_AGGREGATE, 1, s);
-            const size_t vol = (size_t)a.W * a.H * a.Dws;
-            for (int v = 0; v < nviews; ++v)
-                cudaMemsetAsync(a.v[v].S, 0, vol * sizeof(uint16_t), s);
+            // S was cleared by the cost kernel
             if (grad_lut) {
                 MergeArgs m{};
                 m.in_mode = 0;
