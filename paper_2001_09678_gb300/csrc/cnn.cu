@@ -15,7 +15,6 @@ namespace mpv {
 namespace {
 
 constexpr int kTile = 16;          // output tile side of the convolution kernels
-constexpr int kMaxCout = 32;
 
 // out[n][co][y][x] = b[co] + sum_{ci,ky,kx} w[co][ci][ky][kx] in[n][ci][y+ky-1][x+kx-1]
 // (zero padding), optional ReLU; one thread per output pixel and all output channels.
