@@ -120,11 +120,6 @@ __device__ __forceinline__ int path_length(int dx, int dy, int W, int H, int x0,
     return min(nx, ny);
 }
 
-// RM: largest jump |d| handled explicitly.  The penalty of a jump of d labels is
-// eps(d) = min(p1 d, T) for every d <= RM, so whenever the truncation dominates beyond
-// RM (ceil(T/p1) - 1 <= RM) the stencil min over |d| <= RM plus the cap min_v A(v) + T
-// is the full-connectivity minimum.  WIN: the level has per-pixel windows, and the
-// predecessor is re-indexed into the current window through shared memory every step.
 // floor((a + b) / 2) of each 16-bit half (the shift masked so that no bit crosses
 // from the high half into the low half)
 __device__ __forceinline__ uint32_t avg_u16x2(uint32_t a, uint32_t b)
@@ -146,6 +141,13 @@ __device__ __forceinline__ void store_normalised(uint16_t *dst, const uint32_t (
     }
 }
 
+// agg_stencil template parameters.
+// G: lanes per scan path (4 or 8); KW: packed 32-bit words (2 labels each) per lane.
+// RM: largest jump |d| handled explicitly.  The penalty of a jump of d labels is
+// eps(d) = min(p1 d, T) for every d <= RM, so whenever the truncation dominates beyond
+// RM (ceil(T/p1) - 1 <= RM) the stencil min over |d| <= RM plus the cap min_v A(v) + T
+// is the full-connectivity minimum.  WIN: the level has per-pixel windows; a step whose
+// window moved re-indexes the predecessor into the current window through shared memory.
 // BLK: the level is split into independent block_cut x block_cut tiles (a scan path
 // restarts where it enters a new tile); counters track the steps to the next tile edge.
 // LAYER: one layer of the paper's layered merge - the data term is the cost bytes
