@@ -229,7 +229,7 @@ mpv_status mpv_debug_stage(mpv_ctx *ctx, const uint8_t *left, const uint8_t *rig
 mpv_status mpv_level_info(const mpv_ctx *ctx, int32_t width, int32_t height, int32_t level,
                           int32_t *w, int32_t *h, int32_t *range, int32_t *window);
 
-/* ---- Serving: continuous batching over camera streams (spec serving loop) ------
+/* ---- Serving: continuous batching over camera streams (the serving loop) ------
  *
  * A server owns, per registered camera, resident device state (a matcher context whose
  * workspace keeps that frame size's pyramid levels and volumes allocated between frames,
@@ -281,7 +281,7 @@ void mpv_server_destroy(mpv_server *srv);
 
 /* ---- Learned window proposal: network kernels (training and inference) -------------
  *
- * The learned proposal (spec extension; the paper has none) replaces the pyramid's
+ * The learned proposal (an extension; the paper has none) replaces the pyramid's
  * window seeding at the finest level by a small CNN evaluated at the top level: six
  * 3x3 convolutions, zero padding, 2 + D_top input channels (the top level's left and
  * right images and its full-range cost slice), 32 hidden channels with ReLU, one output
