@@ -8,10 +8,14 @@ standing in for the paper's driving sequences.  Metric: Mdisp-evals/s = W*H*D / 
 time (nominal full-range labels of one view), plus fps and p50/p99 latency.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
-                  [--variant plain|paper|gradient|paper_gradient] [--workload frame|batch64]
+                  [--variant plain|paper|gradient|paper_gradient|road|learned|learned16]
+                  [--workload frame|batch64]
 
---variant selects the paper's layered path merge (Section 3.2) and/or the
-gradient-weighted TV penalty (Eq. EU, slopes round(p1 e^{-g/16})) on the same pair.
+--variant selects, on the same pair, the paper's layered path merge (Section 3.2) and/or
+the gradient-weighted TV penalty (Eq. EU, slopes round(p1 e^{-g/16})), the road profile of
+Section 3.5 on the matcher's output (road), or the learned window proposal with a 17- or
+16-label window (learned, learned16).  --workload batch64 times the 64-pair mixed batch
+against the same pairs matched one at a time.
 
 --impl reference times the CPU oracle (single-threaded C) on a bounded sample of the
 same workload: the reference arm of this method is the oracle.  Under torchrun every
