@@ -354,8 +354,15 @@ mpv_status mpv_profile_read(mpv_ctx *ctx, double *ms, int64_t *launches, int32_t
  *     device looks up the array's device address (cudaGetSymbolAddress); make that
  *     first call before any stream capture.
  *   - A pair whose scratch need exceeds MPV_NOALLOC_SCRATCH_BYTES is rejected with
- *     MPV_ERR_INVALID_ARG before anything is launched (640 x 480 at D = 64 with three
- *     scales and the left-right check fits; 1280 x 720 at D = 128 does not).  The
+ *     MPV_ERR_INVALID_ARG before anything is launched.  The need is the one
+ *     mpv_workspace_bytes reports for the same parameters: per view (two with the
+ *     left-right check) and level, two images (width rounded up to 16 bytes) and two
+ *     uint16 maps, plus one cost volume of 1 byte and one summed volume of 2 bytes per
+ *     pixel and label stride (the window rounded up to 16) at the largest level, each
+ *     piece rounded up to 256 bytes; the layered merge (MPV_MERGE_PAPER) adds three more
+ *     2-byte volumes per view.  So 640 x 480 at D = 64 with three scales and the
+ *     left-right check fits with the summed merge (about 34 MB) but not with the layered
+ *     merge (about 93 MB); 1280 x 720 at D = 128 (about 190 MB) does not fit.  The
  *     learned proposal and the right-view output are not available here.
  *   - Every call shares the one array, which keeps the previous call's contents (the
  *     call clears what must start at zero).  Calls that overlap on the GPU (other

@@ -12,6 +12,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import ref  # noqa: E402
 from paper_2001_09678_gb300 import synth  # noqa: E402
 
 
@@ -41,6 +42,9 @@ def _match_with_context(m, params, left, right):
 
 def test_noalloc_matches_context_path_on_consecutive_calls(mpv):
     params = mpv.mpv_default_params(max_disparity=64, num_scales=3, num_paths=8)
+    ora = ref.params(max_disparity=64, num_scales=3, num_paths=8, p1=params.p1,
+                     trunc=params.trunc, window=0, block=(0, 0, 0, 0), lr_check=1, lr_tol=1,
+                     ssim_window=5)
     outs = []
     # two different pairs in a row: the second call reuses the first call's array
     for seed, (W, H) in ((41, (640, 480)), (42, (600, 440))):
@@ -53,6 +57,8 @@ def test_noalloc_matches_context_path_on_consecutive_calls(mpv):
         got = _u16(d)
         want = _match_with_context(mpv, params, left, right)
         assert np.array_equal(got, want), f"{(got != want).sum()} pixels differ"
+        exact = ref.match(L, R, ora)
+        assert np.array_equal(got, exact), f"{(got != exact).sum()} pixels differ from the oracle"
         outs.append(got)
     assert (outs[0] != 0xFFFF).mean() > 0.5
 
