@@ -89,12 +89,22 @@ def test_network_gradients_match_oracle(m):
     acts_dev = [a.float().cpu().numpy().astype(np.float64) for a in acts]
     _, g_ref = cnn_ref.huber(pred.cpu().numpy().astype(np.float64), t, 1.0 / 128)
     grads_ref = cnn_ref.backward(acts_dev, layers, g_ref, round_bf16=True)
-    errs = []
-    for i, ((dw, db), (rw, rb)) in enumerate(zip(grads, grads_ref)):
+    # element by element, against the magnitude of the summed terms: the same chain run on
+    # |activations|, |weights| and |output gradient| (the ReLU masks are unchanged, the
+    # stored activations past a ReLU being >= 0).  FP32 accumulation of at most
+    # N*H*W = 960 terms per weight-gradient element and 288 per data-gradient element,
+    # compounded over the six layers, stays below 2e-4 of that magnitude.
+    layers_abs = [(np.abs(w), np.abs(b), relu) for (w, b, relu) in layers]
+    scales = cnn_ref.backward([np.abs(a) for a in acts_dev], layers_abs, np.abs(g_ref),
+                              round_bf16=True)
+    for i, ((dw, db), (rw, rb), (sw, sb)) in enumerate(zip(grads, grads_ref, scales)):
         dw, db = dw.cpu().numpy(), db.cpu().numpy()
-        errs.append((np.linalg.norm(dw - rw) / np.linalg.norm(rw),
-                     np.linalg.norm(db - rb) / (np.linalg.norm(rb) + 1e-30)))
-    assert all(ew <= 1e-4 and eb <= 1e-4 for ew, eb in errs), errs
+        bad_w = np.abs(dw - rw) > 2e-4 * sw + 1e-12
+        bad_b = np.abs(db - rb) > 2e-4 * sb + 1e-12
+        assert not bad_w.any(), f"layer {i}: {bad_w.sum()} weight-gradient elements off"
+        assert not bad_b.any(), f"layer {i}: {bad_b.sum()} bias-gradient elements off"
+        # and the gradient is not trivially small against its own scale
+        assert np.abs(rw).max() > 1e-3 * sw.max()
 
 
 def test_huber_and_adam(m):
