@@ -568,13 +568,16 @@ int ora_level_range(int D, int S, int l)
     return (D + (1 << sh) - 1) >> sh;
 }
 
-/* The top level covers its full range; the finer levels search a window of Dw
- * labels, Dw = D/4 by default (R15, from Eqs. Ot1 and Ot2).                          */
+/* The top level covers its full range; finer level l searches a window of Dw_l
+ * labels: windows[l-1] when set, else `window`, else D/4 (R15, from Eqs. Ot1 and Ot2,
+ * whose d/4 becomes a width per level in the variable form), clamped to the level's
+ * range D_l.                                                                         */
 int ora_level_window(const ora_params *p, int l)
 {
     const int Dl = ora_level_range(p->max_disparity, p->num_scales, l);
     if (l == 0) return Dl;
-    int Dw = p->window > 0 ? p->window : p->max_disparity / 4;
+    int Dw = p->windows[l - 1] > 0 ? p->windows[l - 1]
+                                    : (p->window > 0 ? p->window : p->max_disparity / 4);
     if (Dw < 1) Dw = 1;
     return Dw < Dl ? Dw : Dl;
 }
@@ -671,7 +674,7 @@ int ora_check_params(int W, int H, const ora_params *p)
     ora_level_dims(W, H, p->num_scales, 0, &W0, &H0);
     if (W0 < N || H0 < N) return -1;
     for (int l = 1; l < p->num_scales; ++l)
-        if (p->block[l - 1] < 0 || p->block[l - 1] > 8) return -1;
+        if (p->block[l - 1] < 0 || p->block[l - 1] > 8 || p->windows[l - 1] < 0) return -1;
     if (p->merge_mode != ORA_MERGE_SUM && p->merge_mode != ORA_MERGE_PAPER) return -1;
     if (p->top_block < 0) return -1;
     if (p->grad_lut)

@@ -40,6 +40,7 @@ typedef struct {
     int32_t merge_mode;     /* ORA_MERGE_SUM or ORA_MERGE_PAPER                    */
     const int32_t *grad_lut;/* NULL, or 256 jump slopes indexed by |I0(p) - I0(p-r)| */
     int32_t top_block;      /* > 0: top level split into independent tiles of this side */
+    int32_t windows[4];     /* Dw of finer level l at index l-1; 0 takes `window`  */
 } ora_params;
 
 /* Integer SSIM constants: round(C1 * n^2), round(C2 * n^2), n = N*N. */

@@ -35,6 +35,7 @@ class OraParams(C.Structure):
         ("merge_mode", C.c_int32),
         ("grad_lut", C.POINTER(C.c_int32)),
         ("top_block", C.c_int32),
+        ("windows", C.c_int32 * 4),
     ]
 
 
@@ -53,7 +54,7 @@ def _lut(grad_lut):
 
 def params(max_disparity=32, num_scales=1, num_paths=4, p1=10, trunc=30, ssim_window=5,
            window=0, block=(0, 0, 0, 0), lr_check=1, lr_tol=1, merge_mode=MERGE_SUM,
-           grad_lut=None, top_block=0):
+           grad_lut=None, top_block=0, windows=(0, 0, 0, 0)):
     p = OraParams()
     p.max_disparity = max_disparity
     p.num_scales = num_scales
@@ -69,6 +70,9 @@ def params(max_disparity=32, num_scales=1, num_paths=4, p1=10, trunc=30, ssim_wi
     p.lr_tol = lr_tol
     p.merge_mode = merge_mode
     p.top_block = top_block
+    win = list(windows) + [0] * (4 - len(windows))
+    for i in range(4):
+        p.windows[i] = win[i]
     p._lut_keep, ptr = _lut(grad_lut)   # the table must outlive the struct's pointer
     if ptr is not None:
         p.grad_lut = ptr
