@@ -112,7 +112,16 @@ def level_geometry():
     return levels
 
 
-def algorithmic_bytes(views=2, variant="plain"):
+ALG_NOTE = {
+    "cost": "images 2 B/px + cost write 1 B/node (cost stored as uint8: exact, costs <= 255)",
+    "aggregate": "cost read 1 B + summed-energy write 2 B per node, window starts 2 B/px "
+                 "(the survey's B_alg reads a uint16 cost: 2 B + 2 B, reported as "
+                 "frac_at_survey_bytes)",
+    "wta": "summed-energy read 2 B/node + window starts and map 2 B/px each",
+}
+
+
+def algorithmic_bytes(views=2, variant="plain", cost_bytes=1):
     """Minimum HBM bytes per frame of each stage: the cost kernel reads both images and
     writes the cost volume (1 B/node: costs are <= 255); the aggregation reads it
     (1 B/node) and writes the uint16 summed volume (2 B/node); winner-take-all reads
@@ -132,13 +141,13 @@ def algorithmic_bytes(views=2, variant="plain"):
     for (w, h, Dl, Dw) in levels:
         n = w * h * Dw
         nodes += n
-        cost += views * (n + 2 * w * h)
+        cost += views * (cost_bytes * n + 2 * w * h)
         img = 2 * w * h if grad else 0          # the reference image, read by the passes
         if merge:
             agg += views * ((2 * n + 4 * n) + (layers - 1) * (8 * n + 4 * n) + img)
             wta += views * (4 * n + 2 * w * h + 2 * w * h)
         else:
-            agg += views * (n + 2 * n + 2 * w * h + img)
+            agg += views * (cost_bytes * n + 2 * n + 2 * w * h + img)
             wta += views * (2 * n + 2 * w * h + 2 * w * h)
     return dict(cost=cost, aggregate=agg, wta=wta), nodes
 
@@ -232,21 +241,31 @@ def code_hash(path):
     return hashlib.sha256(code.encode("utf-8")).hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
-    kernel's code changed since the capture."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+def measured_counters(kernel):
+    """Per-frame device-time-weighted ALU-pipe and issue-slot activity and DRAM bytes of
+    `kernel`'s launches from the committed ncu summary, or None when the kernel's code
+    changed since the capture (the file's code hash no longer matches)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_counters.txt")
     if not os.path.exists(path):
         return None
+    rows, src_ok = [], None
     for line in open(path):
         if line.startswith("#") or "=" not in line:
             continue
         kv = dict(f.split("=", 1) for f in line.split())
-        src = os.path.join(ROOT, kv["source"])
-        if not os.path.exists(src):
-            return None
-        return int(kv["bytes_per_launch"]) if code_hash(src) == kv["code_sha256_16"] else None
-    return None
+        if "code_sha256_16" in kv:
+            src = os.path.join(ROOT, kv["source"])
+            src_ok = os.path.exists(src) and code_hash(src) == kv["code_sha256_16"]
+            continue
+        rows.append({k: float(v) for k, v in kv.items() if k != "level"})
+    if not src_ok or not rows:
+        return None
+    t = sum(r["us"] for r in rows)
+    return {"alu_pipe_active": round(sum(r["alu_pct"] * r["us"] for r in rows) / t / 100, 4),
+            "issue_active": round(sum(r["issue_pct"] * r["us"] for r in rows) / t / 100, 4),
+            "dram_bytes_per_step": int(sum(r["dram_bytes"] for r in rows)),
+            "launches": len(rows),
+            "source": f"profiles/{kernel}_counters.txt (ncu, one frame's launches)"}
 
 
 def measured_peaks():
@@ -378,13 +397,18 @@ def run_mine(args):
 
     # roofline of the dominant kernel (by device time over the timed region)
     alg, nodes = algorithmic_bytes(variant=args.variant)
+    alg4, _ = algorithmic_bytes(variant=args.variant, cost_bytes=2)
     stage_ms = {k: v[0] for k, v in prof.items()}
     launches_per_frame = sum(v[1] for v in prof.values()) / prof_steps
     dom = max(("cost", "aggregate", "wta"), key=lambda k: stage_ms[k])
     peak, peak_kind = measured_peaks()
     dom_s = stage_ms[dom] / 1e3
     achieved = alg[dom] * prof_steps / dom_s / 1e9 if dom_s > 0 else 0.0
+    achieved4 = alg4[dom] * prof_steps / dom_s / 1e9 if dom_s > 0 else 0.0
     kern_launches = prof[dom][1]
+    per_step_launches = kern_launches / prof_steps
+    counters = measured_counters(dom) if args.variant == "plain" else None
+    traffic_step = counters["dram_bytes_per_step"] if counters else None
 
     out = None
     if rank == 0:
@@ -401,17 +425,30 @@ def run_mine(args):
             "fps": round(1e3 / ms_per_step, 1),
             "latency_ms": {"p50": round(statistics.median(step_ms), 4),
                            "p99": round(sorted(step_ms)[min(len(step_ms) - 1,
-                                                            int(0.99 * len(step_ms)))], 4)},
+                                                            int(0.99 * len(step_ms)))], 4),
+                           "samples": len(step_ms)},
             "evaluated_nodes_per_view": nodes,
             "stage_ms_per_step": {k: round(v / prof_steps, 4) for k, v in stage_ms.items()},
             "stage_profile": f"{prof_steps} further frames with per-stage events",
             **({"road_ms_per_step": round(road_ms, 4)} if road_ms is not None else {}),
-            "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
-                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "peak_source": peak_kind,
-                         "alg_bytes_per_step": alg[dom], "launches_per_step":
-                             kern_launches / prof_steps,
-                         "traffic": measured_traffic(dom) if args.variant == "plain" else None},
+            "roofline": {
+                "kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": peak_kind,
+                # traffic and the algorithmic bytes per launch (the frame's launches, one
+                # per pyramid level, averaged), and per step with their ratio
+                "traffic": (int(traffic_step / per_step_launches) if traffic_step else None),
+                "alg_bytes_per_launch": int(alg[dom] / per_step_launches),
+                "alg_bytes_per_step": alg[dom], "launches_per_step": per_step_launches,
+                "traffic_per_step": traffic_step,
+                "traffic_over_alg": (round(traffic_step / alg[dom], 2) if traffic_step else None),
+                "alg_bytes_per_node": ALG_NOTE[dom],
+                "frac_at_survey_bytes": round(achieved4 / peak, 4),
+                # the integer path's second bound: ALU-pipe and issue-slot activity of the
+                # same kernel (ncu, device-time weighted over the frame's launches)
+                "int_pipe": (dict(alu_pipe_active=counters["alu_pipe_active"],
+                                  issue_active=counters["issue_active"],
+                                  source=counters["source"]) if counters else None)},
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
                     "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
                     "ms_per_step": round(1e3 * e2e_s / args.steps, 4),
@@ -425,6 +462,8 @@ def run_mine(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+    if rank == 0 and world == 1 and not args.no_extras and args.variant == "plain":
+        out["extras"] = bench_extras(dev, L, R, ms_per_step)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not lw:
         # (the oracle has no network: the learned variants report no CPU baseline)
         out["cpu_baseline"] = cpu_baseline_full(L, R, args.variant)
@@ -443,17 +482,37 @@ def _ora_params(variant="plain"):
                       grad_lut=gradient_table() if grad else None, **PARAMS)
 
 
-def cpu_baseline_full(L, R, variant="plain"):
-    """The oracle, single-threaded, on one full pair of the workload (both views)."""
+def _oracle_pair(job):
+    """One full pair through the oracle in a worker process; returns its seconds."""
+    L, R, variant = job
     from oracle import ref
     p = _ora_params(variant)
     ref.lib()
     t = time.perf_counter()
     ref.match(L, R, p)
-    dt = time.perf_counter() - t
-    return {"value": round(nominal_units() / dt / 1e6, 3), "unit": UNIT, "cores": 1,
-            "kind": "oracle", "sample": "one full 1280x720 pair, 3 scales, both views",
-            "seconds": round(dt, 2)}
+    return time.perf_counter() - t
+
+
+def cpu_baseline_full(L, R, variant="plain"):
+    """The oracle (single-threaded C) on the machine's host cores: one full pair of the
+    workload (both views) on one core, then one full pair in each of nproc independent
+    processes at once (their aggregate throughput is the reported value)."""
+    import multiprocessing as mp
+    dt1 = _oracle_pair((L, R, variant))
+    n = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        pool.map(_oracle_pair, [(L[:40], R[:40], variant)] * n)    # workers up, oracle loaded
+        t = time.perf_counter()
+        per = pool.map(_oracle_pair, [(L, R, variant)] * n, chunksize=1)
+        wall = time.perf_counter() - t
+    return {"value": round(n * nominal_units() / wall / 1e6, 3), "unit": UNIT, "cores": n,
+            "kind": "oracle",
+            "sample": f"{n} independent processes (one per host core), each one full "
+                      "1280x720 pair, 3 scales, both views",
+            "seconds": round(wall, 2), "per_process_s_max": round(max(per), 2),
+            "single_core": {"value": round(nominal_units() / dt1 / 1e6, 3), "cores": 1,
+                            "seconds": round(dt1, 2),
+                            "sample": "one full 1280x720 pair on one core"}}
 
 
 def run_reference(args):
@@ -501,8 +560,9 @@ def run_reference(args):
     }), flush=True)
 
 
-def run_batch64(args):
-    """Throughput of the 64-pair mixed-resolution batch (one cached CUDA graph)."""
+def measure_batch64(steps, warmup, serial=True):
+    """The 64-pair mixed-resolution batch (one cached CUDA graph per batch): ms per
+    batch, and optionally the same pairs matched one mpv_match at a time."""
     import multiprocessing as mp
     import torch
     from paper_2001_09678_gb300 import synth
@@ -527,29 +587,111 @@ def run_batch64(args):
     mpv.mpv_match_batch(ctx, pairs, stream)     # autotune + capture
     mpv.mpv_sync(ctx)
     setup_s = time.perf_counter() - t
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         mpv.mpv_match_batch(ctx, pairs, stream)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         mpv.mpv_match_batch(ctx, pairs, stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     mpv.mpv_destroy(ctx)
-    seq_ms = _serial_ms(mpv, pairs, stream, max(1, args.steps // 4), args.warmup)
+    out = {"value": round(units / ms / 1e3, 1), "unit": UNIT, "ms_per_batch": round(ms, 3),
+           "pairs_per_s": round(64e3 / ms, 1), "steps": steps, "warmup": warmup,
+           "setup_s": round(setup_s, 2)}
+    if serial:
+        seq_ms = _serial_ms(mpv, pairs, stream, max(1, steps // 4), warmup)
+        out.update({"serial_ms_per_64_pairs": round(seq_ms, 3),
+                    "batch_speedup": round(seq_ms / ms, 2),
+                    "serial": "the same pairs one mpv_match at a time on one stream; per size "
+                              "class one context and one input/output buffer set (each pair "
+                              "copied in on the device first), so every call replays that "
+                              "class's cached graph"})
+    return out
+
+
+def run_batch64(args):
+    """Throughput of the 64-pair mixed-resolution batch (one cached CUDA graph)."""
+    res = measure_batch64(args.steps, args.warmup)
     print(json.dumps({
-        "metric": "Mdisp-evals/s, 64-pair mixed batch", "value": round(units / ms / 1e3, 1),
-        "unit": UNIT, "ms_per_batch": round(ms, 3), "pairs_per_s": round(64e3 / ms, 1),
-        "serial_ms_per_64_pairs": round(seq_ms, 3), "batch_speedup": round(seq_ms / ms, 2),
-        "serial": "the same pairs one mpv_match at a time on one stream; per size class one "
-                  "context and one input/output buffer set (each pair copied in on the "
-                  "device first), so every call replays that class's cached graph",
-        "steps": args.steps, "warmup": args.warmup, "setup_s": round(setup_s, 2),
+        "metric": "Mdisp-evals/s, 64-pair mixed batch", **res,
         "config": {"workload": "16x640x480 D64 + 32x1280x720 D128 + 16x1920x1080 D192, "
                                "3 scales, 8 paths, LR, one CUDA graph per batch"},
     }), flush=True)
+
+
+def bench_extras(dev, L, R, plain_ms):
+    """The other configurations of the workload list, bounded in time and measured on
+    the same GPU beside the headline: the learned window proposal (17- and 16-label
+    windows, the committed network, its bad-pixel rate against full-range single-scale
+    MPV on the bench pair), the 64-pair mixed batch, and the 8-camera served stream
+    (plain and with the learned proposal where the network fits)."""
+    import numpy as np
+    import torch
+    from paper_2001_09678_gb300 import mpv, serve
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    left = torch.from_numpy(L).to(dev)
+    right = torch.from_numpy(R).to(dev)
+    disp = torch.empty((H, W), dtype=torch.int16, device=dev)
+    full = mpv.mpv_create(dev.index)
+    mpv.mpv_set_params(full, mpv.mpv_default_params(**dict(PARAMS, num_scales=1)))
+    mpv.mpv_match(full, left, right, disp, stream)
+    mpv.mpv_sync(full)
+    ref_map = disp.cpu().numpy().view(np.uint16).copy()
+    mpv.mpv_destroy(full)
+    for lw in (17, 16):
+        ctx = mpv.mpv_create(dev.index)
+        mpv.mpv_set_params(ctx, mpv.mpv_default_params(
+            proposal=mpv.MPV_PROPOSAL_LEARNED, window=lw, **PARAMS))
+        mpv.mpv_load_proposal_weights(ctx, WEIGHTS)
+        for _ in range(10):
+            mpv.mpv_match(ctx, left, right, disp, stream)
+        mpv.mpv_sync(ctx)
+        n = 200
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        for a, b in ev:
+            flush.fill_(1)
+            a.record(stream)
+            mpv.mpv_match(ctx, left, right, disp, stream)
+            b.record(stream)
+        mpv.mpv_sync(ctx)
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        got = disp.cpu().numpy().view(np.uint16)
+        both = (got != 0xFFFF) & (ref_map != 0xFFFF)
+        bad = float((np.abs(got.astype(int) - ref_map.astype(int)) > 1)[both].mean())
+        hits, px = mpv.mpv_proposal_stats(ctx)
+        frames, falls = mpv.mpv_proposal_fallbacks(ctx)
+        mpv.mpv_destroy(ctx)
+        out[f"learned{lw}"] = {
+            "ms_per_step": round(sum(ms) / n, 4), "p50_ms": round(ms[n // 2], 4),
+            "p99_ms": round(ms[int(0.99 * n)], 4), "samples": n,
+            "vs_plain_ms": round(plain_ms, 4),
+            "bad_pixel_rate_vs_full_range": round(bad, 5),
+            "edge_hit_rate": round(hits / max(1, px), 4),
+            "fallbacks": falls, "frames": frames,
+            "workload": f"the bench pair, learned proposal (committed network), finest window "
+                        f"{lw}, default fallback (pyramid above 15 % edge hits), L2 flushed"}
+    out["batch64"] = measure_batch64(5, 2, serial=False)
+    out["batch64"]["workload"] = ("16x640x480 D64 + 32x1280x720 D128 + 16x1920x1080 D192, "
+                                  "3 scales, 8 paths, LR, one CUDA graph per batch")
+    cams = serve.camera_specs()
+    pools = serve.frame_pools(sorted({(w, h, d) for _, w, h, d in cams}), 4)
+    for name, prop in (("serving", None), ("serving_learned", WEIGHTS)):
+        r = serve.run(cams, pools, seconds=3.0, hz=30.0, proposal=prop)
+        out[name] = {k: (round(r[k], 4) if isinstance(r[k], float) else r[k])
+                     for k in ("frames", "ok", "fps", "p50_ms", "p99_ms", "max_ms",
+                               "peak_inflight")}
+        out[name]["samples"] = r["ok"]
+        out[name]["workload"] = ("8 cameras (2x640x480 D64, 4x1280x720 D128, 2x1920x1080 "
+                                 "D192), Poisson 30 Hz each, 3 s, latency arrival to map in "
+                                 "host memory" + (", learned proposal on the D128 cameras"
+                                                  if prop else ""))
+    return out
 
 
 def _serial_ms(mpv, pairs, stream, steps, warmup):
@@ -601,6 +743,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("mine", "reference"), default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the learned, batched and served configurations")
     ap.add_argument("--workload", choices=("frame", "batch64"), default="frame",
                     help="frame: the 1280x720 D=128 pair (default); batch64: the mixed batch")
     ap.add_argument("--variant", choices=tuple(VARIANTS), default="plain",

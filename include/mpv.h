@@ -63,6 +63,9 @@ typedef enum {
                                 /* left-to-right pass charges upward jumps twice           */
 #define MPV_PROPOSAL_PYRAMID 0  /* finer-level windows from the coarser level (Sec. 3.4) */
 #define MPV_PROPOSAL_LEARNED 1  /* finest-level windows from the learned proposal        */
+#define MPV_FALLBACK_NONE 0     /* learned proposal: keep its result whatever its windows */
+#define MPV_FALLBACK_PYRAMID 1  /* ... re-match the frame with the pyramid (Sec. 3.4)     */
+#define MPV_FALLBACK_FULL 2     /* ... re-match it at full range, one scale (exact MPV)   */
 
 /* Matcher parameters.  Fill with mpv_default_params, then override. */
 typedef struct {
@@ -85,6 +88,15 @@ typedef struct {
     int32_t top_block;      /* > 0: the top pyramid level is split into independent tiles  */
                             /* of top_block x top_block pixels, MPV per tile (Section 3.4, */
                             /* read literally); 0 (default): the whole top level           */
+    int32_t windows[4];     /* per-level window Dw of levels 1..S-1 (index l-1), each >= 0; */
+                            /* 0 (default) takes `window` (Eqs. Ot1, Ot2 with their d/4    */
+                            /* replaced by a width of the caller's choice per level)       */
+    int32_t fallback;       /* learned proposal only: MPV_FALLBACK_PYRAMID (default),      */
+                            /* MPV_FALLBACK_FULL or MPV_FALLBACK_NONE                      */
+    int32_t fallback_edge_bp; /* the frame is re-matched when more than this many of every */
+                            /* 10000 matched pixels (both views) have their winning label  */
+                            /* on an edge of the proposed window while the range goes on   */
+                            /* past it; 0..10000, default 1500 (15 %)                      */
 } mpv_params;
 
 /* One stereo pair of a batch.  All pointers are device pointers. */
@@ -200,9 +212,21 @@ mpv_status mpv_proposal_predict(mpv_ctx *ctx, const uint8_t *left, const uint8_t
 
 /* Of the last mpv_match with the learned proposal (read after mpv_sync): the pixels
  * whose winning label sits on their window's edge while the range continues past it,
- * and the pixels matched (both views).  A high ratio means the windows missed: the
- * caller should match the pair again with the pyramid (the fallback).                 */
+ * and the pixels matched (both views), both counted on the network's windows.  A high
+ * ratio means the windows missed; with fallback != MPV_FALLBACK_NONE the match itself
+ * then re-matched the frame on the device (see fallback_edge_bp), and the output is
+ * that of the fallback method.                                                        */
 mpv_status mpv_proposal_stats(const mpv_ctx *ctx, uint64_t *edge_hits, uint64_t *pixels);
+
+/* Learned-proposal frames matched by this context with a fallback configured (each
+ * takes the decision) and how many of them fell back (read after mpv_sync; cumulative
+ * since the context's creation).  The decision is taken on the device after the learned
+ * frame's winner-take-all, so the call stays asynchronous: in the frame's cached CUDA
+ * graph the fallback is the body of a conditional node that the decision sets (nothing
+ * runs when it is not needed); launched directly (profiling, MPV_NO_GRAPHS, batches)
+ * the fallback's launches are enqueued behind the decision and return at once unless
+ * it opened them.                                                                     */
+mpv_status mpv_proposal_fallbacks(const mpv_ctx *ctx, uint64_t *frames, uint64_t *fallbacks);
 
 /* Waits for the context's last submitted work and returns any latched device error. */
 mpv_status mpv_sync(mpv_ctx *ctx);

@@ -176,6 +176,7 @@ __device__ __forceinline__ void store_normalised(uint16_t *dst, const uint32_t (
 template <int G, int KW, int RM, bool WIN, bool BLK, bool LAYER, bool SWP, bool XM>
 __global__ void __launch_bounds__(kStencilWarps * 32) agg_stencil(LevelArgs a, MergeArgs mg)
 {
+    if (a.gate && *a.gate == 0) return;
     constexpr int kG = G;                    // lanes per scan path
     constexpr int kPathsPerWarp = 32 / kG;
     constexpr int HW = RM / 2;               // halo words per side
@@ -734,6 +735,7 @@ constexpr int kScanWarps = 8;
 template <int K>
 __global__ void __launch_bounds__(kScanWarps * 32) agg_general(LevelArgs a, MergeArgs m)
 {
+    if (a.gate && *a.gate == 0) return;
     constexpr int NJ = 32 * K;                // labels covered by the warp
     const int view = blockIdx.z;
     const int dir = m.dir0 + blockIdx.y;
@@ -1006,6 +1008,7 @@ __device__ __forceinline__ void scan8_suffix(const int (&A)[K], int slope, int g
 template <int K, bool WIN>
 __global__ void __launch_bounds__(kScan8Warps * 32) agg_scan8(LevelArgs a, MergeArgs m)
 {
+    if (a.gate && *a.gate == 0) return;
     constexpr int G = 8, PPW = 32 / G, DWP = G * K, NJ = DWP;
     constexpr int PF = 4;                    // prefetch distance (steps)
     constexpr int QW = K / 2;                // 32-bit words of one u16 volume per lane

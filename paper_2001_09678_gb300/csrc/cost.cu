@@ -128,6 +128,7 @@ __device__ __forceinline__ uint2 pack_column(const uint8_t *img, int pitch, int 
 template <int N>
 __global__ void __launch_bounds__(kCostThreads) cost_kernel(LevelArgs a, int uspan_max)
 {
+    if (a.gate && *a.gate == 0) return;
     constexpr int R = N / 2;
     constexpr int n = N * N;
     constexpr int NR = 2 * R + 1;          // ring of column products

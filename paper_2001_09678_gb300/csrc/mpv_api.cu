@@ -51,7 +51,10 @@ struct mpv_ctx {
     // learned proposal
     ProposalNet net;
     void *net_mem = nullptr;
-    unsigned long long *edge_host = nullptr;   // pinned: window-edge hits, pixels
+    // pinned: window-edge hits and pixels of the last learned frame, learned frames and
+    // fallbacks since creation (copied from counters_dev after every learned frame)
+    unsigned long long *edge_host = nullptr;
+    unsigned long long *counters_dev = nullptr;   // device: learned frames, fallbacks
     // gradient-weighted penalty: host copy and device copy of the 256 slopes
     bool grad_on = false;
     int32_t grad_host[256] = {};
@@ -336,7 +339,7 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
         const int i = order[r];
         const int w = worker[i];
         est = enqueue_pair(ctx->p, jobs[i], (uint8_t *)ctx->bws + woff[w], ctx->workers[w],
-                           nullptr, nullptr, tune[i], &ctx->net, ctx->lut());
+                           nullptr, nullptr, tune[i], &ctx->net, ctx->lut(), ctx->counters_dev);
     }
     for (int w = 0; w < nw; ++w) {
         cudaEventRecord(ctx->joins[w], ctx->workers[w]);
@@ -367,14 +370,21 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
 // The launches of one pair on stream s with the context's workspace (and, for the
 // learned proposal, the copy of the window-edge counters to pinned host memory).
 mpv_status enqueue_direct(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const StageSink *dbg,
-                          const Tuning &t, const Layout &L)
+                          const Tuning &t, const Layout &L, cudaStream_t aux = nullptr)
 {
     StageHook hook{hook_begin, hook_end, ctx};
-    mpv_status r =
-        enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t, &ctx->net, ctx->lut());
+    mpv_status r = enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, &hook, dbg, t, &ctx->net,
+                                ctx->lut(), ctx->counters_dev, nullptr, aux);
     if (r == MPV_OK && ctx->p.proposal == MPV_PROPOSAL_LEARNED && !dbg) {
-        cudaMemcpyAsync(ctx->edge_host, (uint8_t *)ctx->ws + L.edge,
-                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        // with a fallback the workspace's counters may be reused by the fallback's
+        // launches: the decision keeps its own copy
+        const uint8_t *src = (const uint8_t *)ctx->ws + L.edge;
+        if (ctx->p.fallback != MPV_FALLBACK_NONE)
+            src = (const uint8_t *)ctx->ws + L.gate + offsetof(FallbackGate, hits);
+        cudaMemcpyAsync(ctx->edge_host, src, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(ctx->edge_host + 2, ctx->counters_dev, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s);
         r = cuda_status(cudaGetLastError());
     }
     return r;
@@ -397,11 +407,20 @@ mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const Stage
     const bool learned = ctx->p.proposal == MPV_PROPOSAL_LEARNED;
     if (learned && !ctx->net.layers) return MPV_ERR_INVALID_ARG;    // no weights loaded
     if (learned && !dbg && !ctx->edge_host) {
-        if (cudaMallocHost(&ctx->edge_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        if (cudaMallocHost(&ctx->edge_host, 4 * sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
             return MPV_ERR_OOM;
         }
-        ctx->edge_host[0] = ctx->edge_host[1] = 0;
+        for (int i = 0; i < 4; ++i) ctx->edge_host[i] = 0;
+        if (cudaMalloc(&ctx->counters_dev, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMemset(ctx->counters_dev, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(ctx->edge_host);
+            ctx->edge_host = nullptr;
+            if (ctx->counters_dev) cudaFree(ctx->counters_dev);
+            ctx->counters_dev = nullptr;
+            return MPV_ERR_OOM;
+        }
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (dbg || ctx->profiling || !ctx->single_graphs ||
@@ -429,7 +448,9 @@ mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const Stage
         cudaGetLastError();
         return enqueue_direct(ctx, job, s, dbg, t, L);
     }
-    const mpv_status est = enqueue_direct(ctx, job, ctx->cap, nullptr, t, L);
+    // (a learned-proposal fallback becomes a conditional node, its body captured on the
+    // first worker stream)
+    const mpv_status est = enqueue_direct(ctx, job, ctx->cap, nullptr, t, L, ctx->workers[0]);
     e = cudaStreamEndCapture(ctx->cap, &graph);
     if (e != cudaSuccess || est != MPV_OK) {
         cudaGetLastError();
@@ -487,6 +508,8 @@ mpv_status mpv_default_params(mpv_params *p)
     p->merge_mode = MPV_MERGE_SUM;
     p->proposal = MPV_PROPOSAL_PYRAMID;
     p->top_block = 0;
+    p->fallback = MPV_FALLBACK_PYRAMID;
+    p->fallback_edge_bp = 1500;
     return MPV_OK;
 }
 
@@ -816,6 +839,14 @@ mpv_status mpv_proposal_stats(const mpv_ctx *ctx, uint64_t *edge_hits, uint64_t 
     return MPV_OK;
 }
 
+mpv_status mpv_proposal_fallbacks(const mpv_ctx *ctx, uint64_t *frames, uint64_t *fallbacks)
+{
+    if (!ctx) return MPV_ERR_INVALID_ARG;
+    if (frames) *frames = ctx->edge_host ? ctx->edge_host[2] : 0;
+    if (fallbacks) *fallbacks = ctx->edge_host ? ctx->edge_host[3] : 0;
+    return MPV_OK;
+}
+
 mpv_status mpv_sync(mpv_ctx *ctx)
 {
     if (!ctx) return MPV_ERR_INVALID_ARG;
@@ -981,6 +1012,7 @@ void mpv_destroy(mpv_ctx *ctx)
         if (ctx->grad_dev) cudaFree(ctx->grad_dev);
         if (ctx->road_scratch) cudaFree(ctx->road_scratch);
         if (ctx->edge_host) cudaFreeHost(ctx->edge_host);
+        if (ctx->counters_dev) cudaFree(ctx->counters_dev);
     }
     if (ctx->ws || ctx->stage) {
         DeviceGuard guard(ctx->device);

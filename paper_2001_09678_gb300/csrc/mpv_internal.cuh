@@ -52,6 +52,7 @@ struct LevelArgs {
     unsigned long long *edge;  // optional [2]: WTA at a window edge inside the range, pixels
     int block_cut;   // > 0: independent block_cut x block_cut tiles (scan paths restart)
     int zero_s;      // the cost kernel also clears S (the summed merge accumulates into it)
+    const int *gate; // optional device word: 0 = every kernel of this level returns at once
 };
 
 // Launch shapes chosen per image shape by the autotuner.
@@ -65,6 +66,7 @@ struct SeedArgs {
     int nviews;
     const uint16_t *dprev[kMaxViews];
     uint16_t *lo[kMaxViews];
+    const int *gate;   // as LevelArgs::gate
 };
 
 struct ImageJob {       // one 2x2 down-sampling or mirror job
@@ -74,8 +76,11 @@ struct ImageJob {       // one 2x2 down-sampling or mirror job
     int dst_pitch;
 };
 
-void launch_mirror(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s);
-void launch_down2(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s);
+// gate (optional device word): 0 = the launch does nothing
+void launch_mirror(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s,
+                   const int *gate = nullptr);
+void launch_down2(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s,
+                  const int *gate = nullptr);
 
 struct PyrJob {         // the next two pyramid levels of one image (pyramid2_kernel)
     const uint8_t *src;  // source level, W x H
@@ -88,7 +93,8 @@ struct PyrJob {         // the next two pyramid levels of one image (pyramid2_ke
     uint8_t *d2;         // optional: the level below that
     int p2;
 };
-void launch_pyramid2(const PyrJob *jobs, int njobs, int W, int H, cudaStream_t s);
+void launch_pyramid2(const PyrJob *jobs, int njobs, int W, int H, cudaStream_t s,
+                     const int *gate = nullptr);
 void launch_seed(const SeedArgs &a, cudaStream_t s);
 void launch_cost(const LevelArgs &a, cudaStream_t s);
 void launch_aggregate(const LevelArgs &a, cudaStream_t s);
@@ -110,7 +116,7 @@ int launch_layer(const LevelArgs &a, const MergeArgs &m, cudaStream_t s);
 void launch_wta(const LevelArgs &a, cudaStream_t s);
 void launch_lr(const uint16_t *dL, const uint16_t *dRm, int W, int H, int tol, int check,
                uint16_t *out, int out_pitch, uint16_t *out_right, int right_pitch,
-               cudaStream_t s);
+               cudaStream_t s, const int *gate = nullptr);
 // stage dumps: C (u8, stride Dws) -> u16 [.][Dw]; S (u16, stride Dws) -> u32 [.][Dw]
 void launch_unpack(const LevelArgs &a, int view, uint16_t *cost, uint32_t *sum, cudaStream_t s);
 
@@ -174,7 +180,22 @@ struct Layout {
     size_t X[kMaxViews][3] = {};                  // layered merge: three more volumes per view
     size_t feat = 0, act0 = 0, act1 = 0, q = 0;   // learned proposal (both views)
     size_t edge = 0;                              // edge-hit counters
+    size_t gate = 0;   // learned proposal with a fallback: FallbackGate, past both layouts
 };
+
+// The learned proposal's fallback decision of one frame (device memory).
+struct FallbackGate {
+    int open;                       // 1: the fallback's launches run
+    int pad;
+    unsigned long long hits, px;    // the learned frame's window-edge counters
+};
+// cond (optional): the IF node of a captured graph whose body holds the fallback; the
+// decision also sets that node's condition
+void launch_fallback_gate(const unsigned long long *edge, int edge_bp, FallbackGate *gate,
+                          unsigned long long *counters, cudaStream_t s,
+                          const cudaGraphConditionalHandle *cond = nullptr);
+// Parameters of the fallback matcher of a learned-proposal configuration.
+mpv_params fallback_params(const mpv_params &p);
 
 struct PairJob {
     const uint8_t *left, *right;
@@ -209,10 +230,15 @@ int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg);
 
 // Enqueues the whole matcher for one pair on stream s, with its scratch at `workspace`
 // (at least make_layout(...).total bytes).
+// counters (optional, device): learned frames and fallbacks, added to by the decision.
+// gate (optional, device): the whole pair's launches return at once while *gate == 0.
+// aux (optional): with s capturing a CUDA graph, the learned proposal's fallback goes into
+// the body of a conditional node (captured on aux) instead of gated launches.
 mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *workspace,
                         cudaStream_t s, const StageHook *hook, const StageSink *dbg,
                         const Tuning &tune = Tuning(), const ProposalNet *net = nullptr,
-                        const int *grad_lut = nullptr);
+                        const int *grad_lut = nullptr, unsigned long long *counters = nullptr,
+                        const int *gate = nullptr, cudaStream_t aux = nullptr);
 // The context's loaded proposal network fits a range of D labels.
 bool proposal_fits(const mpv_ctx *ctx, int D);
 

@@ -54,13 +54,26 @@ bool params_valid(const mpv_params &p)
     if (p.proposal != MPV_PROPOSAL_PYRAMID && p.proposal != MPV_PROPOSAL_LEARNED) return false;
     if (p.top_block < 0) return false;
     for (int i = 0; i < 4; ++i)
-        if (p.block[i] < 0 || p.block[i] > 8) return false;
+        if (p.block[i] < 0 || p.block[i] > 8 || p.windows[i] < 0) return false;
+    if (p.fallback != MPV_FALLBACK_NONE && p.fallback != MPV_FALLBACK_PYRAMID &&
+        p.fallback != MPV_FALLBACK_FULL)
+        return false;
+    if (p.fallback_edge_bp < 0 || p.fallback_edge_bp > 10000) return false;
     return true;
+}
+
+mpv_params fallback_params(const mpv_params &p)
+{
+    mpv_params q = p;
+    q.proposal = MPV_PROPOSAL_PYRAMID;
+    q.fallback = MPV_FALLBACK_NONE;
+    if (p.fallback == MPV_FALLBACK_FULL) q.num_scales = 1;   // exact MPV over the full range
+    return q;
 }
 
 // Level sizes, ranges and windows (Section 3.4): level S-1 is the input, each level
 // above halves the size (rounding up) and the range; the top level searches its whole
-// range, the others a window of Dw labels (D/4 by default).
+// range, level l > 0 a window of windows[l-1] labels, else `window`, else D/4.
 void make_geometry(const mpv_params &p, int W, int H, int D, Geometry &g)
 {
     g.S = p.num_scales;
@@ -76,7 +89,8 @@ void make_geometry(const mpv_params &p, int W, int H, int D, Geometry &g)
     int Dw = p.window > 0 ? p.window : D / 4;
     if (Dw < 1) Dw = 1;
     for (int l = 0; l < g.S; ++l) {
-        g.Dw[l] = l == 0 ? g.D[0] : (Dw < g.D[l] ? Dw : g.D[l]);
+        const int w = l > 0 && p.windows[l - 1] > 0 ? p.windows[l - 1] : Dw;
+        g.Dw[l] = l == 0 ? g.D[0] : (w < g.D[l] ? w : g.D[l]);
         if (p.proposal == MPV_PROPOSAL_LEARNED && l == g.S - 1 && l > 0)
             g.Dw[l] = learned_window(p, D);
         g.Dws[l] = (g.Dw[l] + 15) / 16 * 16;
@@ -142,6 +156,17 @@ Layout make_layout(const Geometry &g, int nviews, const mpv_params &p)
         L.q = take(off, 2 * sizeof(float) * px0);
     }
     L.edge = take(off, 2 * sizeof(unsigned long long));
+    if (learned && p.fallback != MPV_FALLBACK_NONE) {
+        // the fallback matcher reuses the workspace after the learned frame; the decision
+        // lies past both layouts
+        const mpv_params q = fallback_params(p);
+        const int top = g.S - 1;
+        Geometry gq;
+        make_geometry(q, g.W[top], g.H[top], g.D[top], gq);
+        const Layout Lq = make_layout(gq, nviews, q);
+        if (Lq.total > off) off = Lq.total;
+        L.gate = take(off, sizeof(FallbackGate));
+    }
     L.total = off;
     return L;
 }
@@ -177,9 +202,59 @@ int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg)
     return (p.lr_check || job.disp_right || (dbg && dbg->view == 1)) ? 2 : 1;
 }
 
+namespace {
+
+// The fallback of a learned-proposal frame inside the CUDA graph being captured on s: the
+// decision kernel sets the condition of an IF node whose body (captured on aux) is the
+// fallback matcher, so an untaken fallback costs nothing.
+mpv_status enqueue_fallback_node(const mpv_params &q, const PairJob &job, uint8_t *base,
+                                 cudaStream_t s, cudaStream_t aux, const Tuning &tune,
+                                 const int *grad_lut, const unsigned long long *edge, int edge_bp,
+                                 FallbackGate *fg, unsigned long long *counters)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &graph) != cudaSuccess ||
+        st != cudaStreamCaptureStatusActive || !graph)
+        return MPV_ERR_CUDA;
+    cudaGraphConditionalHandle cond;
+    if (cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) !=
+        cudaSuccess)
+        return MPV_ERR_CUDA;
+    launch_fallback_gate(edge, edge_bp, fg, counters, s, &cond);
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &graph, &deps, nullptr, &ndeps) != cudaSuccess)
+        return MPV_ERR_CUDA;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp) != cudaSuccess)
+        return MPV_ERR_CUDA;
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return MPV_ERR_CUDA;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(aux, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return MPV_ERR_CUDA;
+    const mpv_status r = enqueue_pair(q, job, base, aux, nullptr, nullptr, tune, nullptr,
+                                      grad_lut);
+    cudaGraph_t got = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(aux, &got);
+    if (r != MPV_OK) return r;
+    return e == cudaSuccess ? MPV_OK : MPV_ERR_CUDA;
+}
+
+}  // namespace
+
 mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, cudaStream_t s,
                         const StageHook *hook, const StageSink *dbg, const Tuning &tune,
-                        const ProposalNet *net, const int *grad_lut)
+                        const ProposalNet *net, const int *grad_lut,
+                        unsigned long long *counters, const int *gate, cudaStream_t aux)
 {
     Geometry g;
     make_geometry(p, job.W, job.H, job.D, g);
@@ -215,7 +290,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
         HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
         ImageJob m[2] = {{job.right, job.pitch, base + L.img0[1][top], g.pitch[top]},
                          {job.left, job.pitch, base + L.img1[1][top], g.pitch[top]}};
-        launch_mirror(m, 2, job.W, job.H, s);
+        launch_mirror(m, 2, job.W, job.H, s, gate);
     }
     if (top >= 1) {
         HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
@@ -238,7 +313,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
                 j.d2 = l2 >= 0 ? base + dimg[l2] : nullptr;
                 j.p2 = l2 >= 0 ? g.pitch[l2] : 0;
             }
-        launch_pyramid2(pj, n, job.W, job.H, s);
+        launch_pyramid2(pj, n, job.W, job.H, s, gate);
     }
     for (int l = top - 3; l >= 0; --l) {
         HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
@@ -248,11 +323,11 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             jobs[n++] = {I0[v][l + 1], P0[v][l + 1], base + L.img0[v][l], g.pitch[l]};
             jobs[n++] = {I1[v][l + 1], P1[v][l + 1], base + L.img1[v][l], g.pitch[l]};
         }
-        launch_down2(jobs, n, g.W[l + 1], g.H[l + 1], s);
+        launch_down2(jobs, n, g.W[l + 1], g.H[l + 1], s, gate);
     }
 
     const int last = dbg ? dbg->level : top;
-    if (!dbg) cudaMemsetAsync(edge, 0, 2 * sizeof(unsigned long long), s);
+    if (!dbg && learned) cudaMemsetAsync(edge, 0, 2 * sizeof(unsigned long long), s);
     for (int l = 0; l <= last; ++l) {
         if (learned && l > 0 && l < top) continue;
         LevelArgs a{};
@@ -275,6 +350,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
         a.npaths = p.num_paths;
         a.lanes = tune.lanes;
         a.block_cut = l == 0 ? p.top_block : 0;
+        a.gate = gate;
         for (int v = 0; v < nviews; ++v) {
             ViewLevel &vl = a.v[v];
             vl.I0 = I0[v][l];
@@ -307,6 +383,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             sa.Dw = g.Dw[l];
             sa.D = g.D[l];
             sa.nviews = nviews;
+            sa.gate = gate;
             for (int v = 0; v < nviews; ++v) {
                 sa.dprev[v] = (const uint16_t *)(base + L.d[v][l - 1]);
                 sa.lo[v] = (uint16_t *)(base + L.lo[v][l]);
@@ -417,7 +494,26 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
         const uint16_t *dL = (const uint16_t *)(base + L.d[0][top]);
         const uint16_t *dRm = nviews == 2 ? (const uint16_t *)(base + L.d[1][top]) : dL;
         launch_lr(dL, dRm, job.W, job.H, p.lr_tol, p.lr_check, job.disp, job.disp_pitch,
-                  nviews == 2 ? job.disp_right : nullptr, job.disp_pitch, s);
+                  nviews == 2 ? job.disp_right : nullptr, job.disp_pitch, s, gate);
+        if (learned && p.fallback != MPV_FALLBACK_NONE) {
+            // the exact method as fallback and judge: decided on the device from the
+            // window-edge hits, its launches always enqueued and gated by the decision
+            FallbackGate *fg = (FallbackGate *)(base + L.gate);
+            const mpv_params q = fallback_params(p);
+            const mpv_status v = validate_pair(q, job.W, job.H, job.pitch, job.disp_pitch, job.D);
+            if (v != MPV_OK) return v;
+            if (aux) {
+                const mpv_status r = enqueue_fallback_node(q, job, base, s, aux, tune, grad_lut,
+                                                           edge, p.fallback_edge_bp, fg,
+                                                           counters);
+                if (r != MPV_OK) return r;
+            } else {
+                launch_fallback_gate(edge, p.fallback_edge_bp, fg, counters, s);
+                const mpv_status r = enqueue_pair(q, job, base, s, hook, nullptr, tune, nullptr,
+                                                  grad_lut, nullptr, &fg->open);
+                if (r != MPV_OK) return r;
+            }
+        }
     }
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) return MPV_OK;

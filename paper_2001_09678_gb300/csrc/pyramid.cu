@@ -10,9 +10,9 @@ namespace mpv {
 
 namespace {
 
-__global__ void mirror_kernel(const ImageJob *__restrict__ jobs_unused, ImageJob j0, ImageJob j1,
-                              int W, int H)
+__global__ void mirror_kernel(const int *gate, ImageJob j0, ImageJob j1, int W, int H)
 {
+    if (gate && *gate == 0) return;
     const ImageJob j = blockIdx.z == 0 ? j0 : j1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -29,8 +29,9 @@ struct PyrJobs4 {
 };
 
 // 2x2 box mean, round half up; the last row/column is replicated when odd.
-__global__ void down2_kernel(Jobs4 jobs, int W, int H)
+__global__ void down2_kernel(Jobs4 jobs, int W, int H, const int *gate)
 {
+    if (gate && *gate == 0) return;
     const ImageJob j = jobs.j[blockIdx.z];
     const int W2 = (W + 1) >> 1, H2 = (H + 1) >> 1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -51,8 +52,10 @@ __global__ void down2_kernel(Jobs4 jobs, int W, int H)
 // at each level.  A block makes 64 x 2 pixels of the first level and 32 x 1 of the second.
 constexpr int kPyrCols = 64;
 
-__global__ void __launch_bounds__(2 * kPyrCols) pyramid2_kernel(PyrJobs4 jobs, int W, int H)
+__global__ void __launch_bounds__(2 * kPyrCols) pyramid2_kernel(PyrJobs4 jobs, int W, int H,
+                                                                 const int *gate)
 {
+    if (gate && *gate == 0) return;
     const PyrJob j = jobs.j[blockIdx.z];
     const int W1 = (W + 1) >> 1, H1 = (H + 1) >> 1;
     const int tx = threadIdx.x % kPyrCols, ty = threadIdx.x / kPyrCols;
@@ -98,6 +101,7 @@ __global__ void __launch_bounds__(2 * kPyrCols) pyramid2_kernel(PyrJobs4 jobs, i
 
 __global__ void seed_kernel(SeedArgs a)
 {
+    if (a.gate && *a.gate == 0) return;
     const int view = blockIdx.z;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -155,6 +159,7 @@ __device__ __forceinline__ uint32_t avg_u16x2(uint32_t a, uint32_t b)
 template <int LPP>
 __global__ void wta_kernel(LevelArgs a)
 {
+    if (a.gate && *a.gate == 0) return;
     const int view = blockIdx.z;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = g / LPP;
@@ -252,8 +257,9 @@ __global__ void unpack_kernel(LevelArgs a, int view, uint16_t *cost, uint32_t *s
 // Left-right check.  dRm is the right view's map in mirrored coordinates.
 __global__ void lr_kernel(const uint16_t *__restrict__ dL, const uint16_t *__restrict__ dRm,
                           int W, int H, int tol, int check, uint16_t *out, int out_pitch,
-                          uint16_t *out_right, int right_pitch)
+                          uint16_t *out_right, int right_pitch, const int *gate)
 {
+    if (gate && *gate == 0) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W || y >= H) return;
@@ -273,28 +279,31 @@ __global__ void lr_kernel(const uint16_t *__restrict__ dL, const uint16_t *__res
 
 }  // namespace
 
-void launch_mirror(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s)
+void launch_mirror(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s,
+                   const int *gate)
 {
     dim3 grid((W + 127) / 128, H, njobs);
-    mirror_kernel<<<grid, 128, 0, s>>>(nullptr, jobs[0], njobs > 1 ? jobs[1] : jobs[0], W, H);
+    mirror_kernel<<<grid, 128, 0, s>>>(gate, jobs[0], njobs > 1 ? jobs[1] : jobs[0], W, H);
 }
 
-void launch_down2(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s)
+void launch_down2(const ImageJob *jobs, int njobs, int W, int H, cudaStream_t s,
+                  const int *gate)
 {
     Jobs4 j4;
     for (int i = 0; i < 4; ++i) j4.j[i] = jobs[i < njobs ? i : 0];
     const int W2 = (W + 1) / 2, H2 = (H + 1) / 2;
     dim3 grid((W2 + 127) / 128, H2, njobs);
-    down2_kernel<<<grid, 128, 0, s>>>(j4, W, H);
+    down2_kernel<<<grid, 128, 0, s>>>(j4, W, H, gate);
 }
 
-void launch_pyramid2(const PyrJob *jobs, int njobs, int W, int H, cudaStream_t s)
+void launch_pyramid2(const PyrJob *jobs, int njobs, int W, int H, cudaStream_t s,
+                     const int *gate)
 {
     PyrJobs4 j4;
     for (int i = 0; i < 4; ++i) j4.j[i] = jobs[i < njobs ? i : 0];
     const int W1 = (W + 1) / 2, H1 = (H + 1) / 2;
     dim3 grid((W1 + kPyrCols - 1) / kPyrCols, (H1 + 1) / 2, njobs);
-    pyramid2_kernel<<<grid, 2 * kPyrCols, 0, s>>>(j4, W, H);
+    pyramid2_kernel<<<grid, 2 * kPyrCols, 0, s>>>(j4, W, H, gate);
 }
 
 void launch_seed(const SeedArgs &a, cudaStream_t s)
@@ -323,11 +332,41 @@ void launch_unpack(const LevelArgs &a, int view, uint16_t *cost, uint32_t *sum, 
 
 void launch_lr(const uint16_t *dL, const uint16_t *dRm, int W, int H, int tol, int check,
                uint16_t *out, int out_pitch, uint16_t *out_right, int right_pitch,
-               cudaStream_t s)
+               cudaStream_t s, const int *gate)
 {
     dim3 grid((W + 127) / 128, H, 1);
     lr_kernel<<<grid, 128, 0, s>>>(dL, dRm, W, H, tol, check, out, out_pitch, out_right,
-                                    right_pitch);
+                                    right_pitch, gate);
+}
+
+namespace {
+
+// The fallback decision of a learned-proposal frame: re-match when more than edge_bp of
+// every 10000 matched pixels won on a window edge (one thread).
+__global__ void fallback_gate_kernel(const unsigned long long *edge, int edge_bp,
+                                     FallbackGate *gate, unsigned long long *counters,
+                                     cudaGraphConditionalHandle cond, int has_cond)
+{
+    const unsigned long long hits = edge[0], px = edge[1];
+    const int open = hits * 10000ull > (unsigned long long)edge_bp * px ? 1 : 0;
+    gate->hits = hits;
+    gate->px = px;
+    gate->open = open;
+    if (counters) {
+        atomicAdd(counters, 1ull);
+        if (open) atomicAdd(counters + 1, 1ull);
+    }
+    if (has_cond) cudaGraphSetConditional(cond, (unsigned)open);
+}
+
+}  // namespace
+
+void launch_fallback_gate(const unsigned long long *edge, int edge_bp, FallbackGate *gate,
+                          unsigned long long *counters, cudaStream_t s,
+                          const cudaGraphConditionalHandle *cond)
+{
+    fallback_gate_kernel<<<1, 1, 0, s>>>(edge, edge_bp, gate, counters,
+                                         cond ? *cond : cudaGraphConditionalHandle{}, cond != nullptr);
 }
 
 }  // namespace mpv

@@ -267,8 +267,9 @@ def train(seconds=600.0, out="proposal.bin", capacity=4096, batch=8, steps_per_p
 
 def evaluate(weights, npairs=40, seed0=900000, log=print):
     """Bad-pixel rate (> 1 px) against full-range single-scale MPV of: the pyramid, the
-    trained proposal, an untrained network and a constant-centre network; edge-hit rate
-    and frame time of each."""
+    trained proposal, an untrained network and a constant-centre network, each network on
+    its own windows (no fallback); edge-hit rate and frame time of each, and how many
+    frames each network's matcher re-matches under the default fallback."""
     import multiprocessing as mp
     import os
     import tempfile
@@ -298,10 +299,14 @@ def evaluate(weights, npairs=40, seed0=900000, log=print):
     full = ctx_for(num_scales=1)
     pyr = ctx_for()
     learned = {}
+    defaults = {}      # the same networks with the matcher's default fallback
     for name, p in variants.items():
-        c = ctx_for(proposal=mpv.MPV_PROPOSAL_LEARNED)
+        c = ctx_for(proposal=mpv.MPV_PROPOSAL_LEARNED, fallback=mpv.MPV_FALLBACK_NONE)
         mpv.mpv_load_proposal_weights(c, p)
         learned[name] = c
+        c = ctx_for(proposal=mpv.MPV_PROPOSAL_LEARNED)
+        mpv.mpv_load_proposal_weights(c, p)
+        defaults[name] = c
     stats = {k: dict(bad=0, both=0, edge=0, px=0, ms=0.0, fallback=0)
              for k in ["pyramid"] + list(variants)}
     d_ref = torch.empty((H_TRAIN, W_TRAIN), dtype=torch.int16, device="cuda")
@@ -327,13 +332,22 @@ def evaluate(weights, npairs=40, seed0=900000, log=print):
                 hits, px = mpv.mpv_proposal_stats(c)
                 st["edge"] += hits
                 st["px"] += px
-    for c in [full, pyr] + list(learned.values()):
+        for c in defaults.values():
+            mpv.mpv_match(c, l, r, d)
+        torch.cuda.synchronize()
+    falls = {}
+    for name, c in defaults.items():
+        mpv.mpv_sync(c)
+        falls[name] = mpv.mpv_proposal_fallbacks(c)[1]
+    for c in [full, pyr] + list(learned.values()) + list(defaults.values()):
         mpv.mpv_destroy(c)
     out = {}
     for k, st in stats.items():
         out[k] = dict(bad_pixel_rate=st["bad"] / max(1, st["both"]),
                       edge_hit_rate=(st["edge"] / st["px"]) if st["px"] else None,
                       ms_per_frame=st["ms"] / npairs)
+        if k in falls:
+            out[k]["fallbacks_with_default"] = falls[k]
         log(f"{k:10s} bad>1px {out[k]['bad_pixel_rate']:.4f}  edge {out[k]['edge_hit_rate']}  "
             f"{out[k]['ms_per_frame']:.3f} ms")
     return out

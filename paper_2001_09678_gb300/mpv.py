@@ -28,6 +28,9 @@ MPV_MERGE_SUM = 0
 MPV_MERGE_PAPER = 1
 MPV_PROPOSAL_PYRAMID = 0
 MPV_PROPOSAL_LEARNED = 1
+MPV_FALLBACK_NONE = 0
+MPV_FALLBACK_PYRAMID = 1
+MPV_FALLBACK_FULL = 2
 
 
 class MpvError(RuntimeError):
@@ -52,6 +55,9 @@ class mpv_params(C.Structure):
         ("merge_mode", C.c_int32),
         ("proposal", C.c_int32),
         ("top_block", C.c_int32),
+        ("windows", C.c_int32 * 4),
+        ("fallback", C.c_int32),
+        ("fallback_edge_bp", C.c_int32),
     ]
 
 
@@ -91,6 +97,7 @@ EXPORTS = [
     "mpv_cnn_conv3x3", "mpv_cnn_conv3x3_wgrad", "mpv_cnn_flip_transpose",
     "mpv_cnn_relu_backward", "mpv_cnn_huber", "mpv_cnn_adam", "mpv_cnn_to_bf16",
     "mpv_cnn_target", "mpv_proposal_features", "mpv_proposal_stats", "mpv_proposal_predict",
+    "mpv_proposal_fallbacks",
 ]
 MPV_NOALLOC_SCRATCH_BYTES = 64 << 20
 MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
@@ -151,6 +158,7 @@ def load(path: str = LIB_PATH):
     L.mpv_proposal_predict.argtypes = [ctx, vp, vp, i32, i32, i32, i32, vp, vp]
     L.mpv_proposal_features.argtypes = [ctx, vp, vp, i32, i32, i32, i32, vp, vp]
     L.mpv_proposal_stats.argtypes = [ctx, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+    L.mpv_proposal_fallbacks.argtypes = [ctx, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     L.mpv_destroy.argtypes = [ctx]
     L.mpv_destroy.restype = None
     L.mpv_server_destroy.restype = None
@@ -190,10 +198,11 @@ def mpv_default_params(**overrides) -> mpv_params:
     p = mpv_params()
     _check(load().mpv_default_params(C.byref(p)), "mpv_default_params")
     for k, v in overrides.items():
-        if k == "block":
+        if k in ("block", "windows"):
             blk = list(v) + [0] * (4 - len(v))
+            arr = getattr(p, k)
             for i in range(4):
-                p.block[i] = blk[i]
+                arr[i] = blk[i]
         else:
             setattr(p, k, v)
     return p
@@ -462,6 +471,13 @@ def mpv_proposal_stats(ctx):
     _check(load().mpv_proposal_stats(ctx, C.byref(a), C.byref(b)), "mpv_proposal_stats")
     return a.value, b.value
 
+
+
+def mpv_proposal_fallbacks(ctx):
+    """(learned frames, frames that fell back) since the context's creation."""
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(load().mpv_proposal_fallbacks(ctx, C.byref(a), C.byref(b)), "mpv_proposal_fallbacks")
+    return a.value, b.value
 
 def mpv_destroy(ctx) -> None:
     load().mpv_destroy(ctx)

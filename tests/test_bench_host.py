@@ -28,20 +28,30 @@ def test_algorithmic_bytes():
     assert lay["wta"] - alg["wta"] == 2 * 2 * nodes   # the last pair is read, not one S
 
 
-def test_traffic_is_reported_only_for_the_captured_code(tmp_path, monkeypatch):
-    import os
+def test_counters_are_reported_only_for_the_captured_code(tmp_path, monkeypatch):
     src = tmp_path / "k.cu"
     src.write_text("// what it does\nint k() { return 1; }  // one\n")
     h = bench.code_hash(str(src))
     (tmp_path / "profiles").mkdir()
-    (tmp_path / "profiles" / "k_traffic.txt").write_text(
-        f"# comment\nkernel=k source=k.cu code_sha256_16={h} bytes_per_launch=1234\n")
+    (tmp_path / "profiles" / "k_counters.txt").write_text(
+        f"# comment\nsource=k.cu code_sha256_16={h}\n"
+        "level=0 us=10 dram_bytes=100 alu_pct=40 issue_pct=50\n"
+        "level=1 us=30 dram_bytes=300 alu_pct=80 issue_pct=70\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.measured_traffic("k") == 1234
-    # comments and blank lines edited: the same code, the same traffic
+    c = bench.measured_counters("k")
+    # device-time weighted: (10*40 + 30*80) / 40 = 70 %, (10*50 + 30*70) / 40 = 65 %
+    assert c["alu_pipe_active"] == 0.7 and c["issue_active"] == 0.65
+    assert c["dram_bytes_per_step"] == 400 and c["launches"] == 2
+    # comments and blank lines edited: the same code, the same counters
     src.write_text("/* what\n   it does */\n\nint k() { return 1; }\n// the end\n")
-    assert bench.measured_traffic("k") == 1234
-    src.write_text("int k() { return 2; }\n")         # the code changed: no traffic
-    assert bench.measured_traffic("k") is None
-    assert bench.measured_traffic("absent") is None
-    assert os.path.exists(tmp_path / "profiles" / "k_traffic.txt")
+    assert bench.measured_counters("k")["dram_bytes_per_step"] == 400
+    src.write_text("int k() { return 2; }\n")         # the code changed: nothing reported
+    assert bench.measured_counters("k") is None
+    assert bench.measured_counters("absent") is None
+
+
+def test_survey_bytes_add_one_byte_per_node_read_and_written():
+    a1, nodes = bench.algorithmic_bytes()
+    a2, _ = bench.algorithmic_bytes(cost_bytes=2)
+    assert a2["aggregate"] - a1["aggregate"] == 2 * nodes      # the cost read, both views
+    assert a2["cost"] - a1["cost"] == 2 * nodes                # the cost write

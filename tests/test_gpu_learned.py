@@ -18,6 +18,8 @@ from oracle import cnn_ref, ref  # noqa: E402
 from paper_2001_09678_gb300 import synth  # noqa: E402
 
 KW = dict(max_disparity=64, num_scales=3, num_paths=8, p1=10, trunc=30)
+# the network's own result, not the exact fallback's (tests/test_gpu_fallback.py covers that)
+NOFB = dict(fallback=0)
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +44,7 @@ def test_learned_match_equals_oracle_given_windows(m):
     path, _ = _weights_file(2 + 16, seed=1)
     ctx = m.mpv_create(0)
     try:
-        m.mpv_set_params(ctx, m.mpv_default_params(proposal=m.MPV_PROPOSAL_LEARNED, **KW))
+        m.mpv_set_params(ctx, m.mpv_default_params(proposal=m.MPV_PROPOSAL_LEARNED, **NOFB, **KW))
         m.mpv_load_proposal_weights(ctx, path)
         l, r = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
         d = torch.full(L.shape, -2, dtype=torch.int16, device="cuda")
@@ -97,7 +99,7 @@ def test_learned_requires_weights_and_matching_channels(m):
     L, R, _ = synth.slanted_pair(128, 96, seed=33, d_max=40)
     ctx = m.mpv_create(0)
     try:
-        m.mpv_set_params(ctx, m.mpv_default_params(proposal=m.MPV_PROPOSAL_LEARNED, **KW))
+        m.mpv_set_params(ctx, m.mpv_default_params(proposal=m.MPV_PROPOSAL_LEARNED, **NOFB, **KW))
         l, r = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
         d = torch.zeros(L.shape, dtype=torch.int16, device="cuda")
         with pytest.raises(m.MpvError):          # no network loaded
@@ -122,7 +124,7 @@ def test_pipeline_prediction_equals_the_network_kernels(m):
     ctx = m.mpv_create(0)
     pyr = m.mpv_create(0)
     try:
-        m.mpv_set_params(ctx, m.mpv_default_params(proposal=m.MPV_PROPOSAL_LEARNED, **KW))
+        m.mpv_set_params(ctx, m.mpv_default_params(proposal=m.MPV_PROPOSAL_LEARNED, **NOFB, **KW))
         m.mpv_load_proposal_weights(ctx, path)
         m.mpv_set_params(pyr, m.mpv_default_params(**KW))
         l, r = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
@@ -140,3 +142,41 @@ def test_pipeline_prediction_equals_the_network_kernels(m):
         m.mpv_destroy(ctx)
         m.mpv_destroy(pyr)
         os.unlink(path)
+
+
+def test_full_size_learned_match_equals_oracle_given_windows(m):
+    # the committed network at its own configuration: 1280x720, D = 128, 3 scales, the
+    # finest level searching centre +- 8 (17 labels, a padded 32-label stride)
+    weights = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                           "paper_2001_09678_gb300", "weights", "proposal_d128_s3.bin")
+    L, R, _ = synth.slanted_pair(1280, 720, seed=900123)
+    ctx = m.mpv_create(0)
+    try:
+        m.mpv_set_params(ctx, m.mpv_default_params(proposal=m.MPV_PROPOSAL_LEARNED, **NOFB,
+                                                   max_disparity=128, num_scales=3,
+                                                   num_paths=8, p1=10, trunc=30))
+        m.mpv_load_proposal_weights(ctx, weights)
+        l, r = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+        d = torch.full(L.shape, -2, dtype=torch.int16, device="cuda")
+        m.mpv_match(ctx, l, r, d)
+        m.mpv_sync(ctx)
+        los = []
+        for view in (0, 1):
+            lo = torch.zeros(L.shape, dtype=torch.int16, device="cuda")
+            m.mpv_debug_stage(ctx, l, r, view, 2, lo=lo)
+            los.append(lo.cpu().numpy().view(np.uint16).astype(np.int32))
+        got = d.cpu().numpy().view(np.uint16)
+    finally:
+        m.mpv_destroy(ctx)
+    Dw = 17
+    assert all((lo >= 0).all() and (lo <= 128 - Dw).all() for lo in los)
+    maps = []
+    for view, lo in zip((0, 1), los):
+        I0, I1 = (L, R) if view == 0 else (np.ascontiguousarray(R[:, ::-1]),
+                                           np.ascontiguousarray(L[:, ::-1]))
+        Cv = ref.cost_volume(I0, I1, 5, Dw, lo=lo)
+        S = ref.aggregate(Cv, 8, 10, 30, lo=lo)
+        maps.append(ref.wta(S, lo=lo))
+    want = ref.lr_check(maps[0], maps[1][:, ::-1], 1)
+    assert np.array_equal(got, want), f"{(got != want).sum()} pixels differ"
+    assert (got != 0xFFFF).mean() > 0.6     # occlusions and the image border fail the check

@@ -12,7 +12,7 @@ from oracle import ref  # noqa: E402
 from paper_2001_09678_gb300 import synth  # noqa: E402
 
 ORA_KEYS = ("max_disparity", "num_scales", "num_paths", "p1", "trunc", "ssim_window", "window",
-            "block", "lr_check", "lr_tol", "merge_mode", "top_block")
+            "block", "lr_check", "lr_tol", "merge_mode", "top_block", "windows")
 
 
 @pytest.fixture(scope="module")
@@ -131,6 +131,31 @@ CASES = {
     "tiles_paper_grad": (lambda: synth.slanted_pair(224, 128, seed=74, d_max=56)[:2],
                          dict(max_disparity=64, num_scales=3, num_paths=8, merge_mode=PAPER,
                               top_block=12), exp_table(10, 16)),
+    # a window width per finer level (Section 3.4, the variable form of Eqs. Ot1/Ot2):
+    # strides of 48 and 16 labels, padded strides, the layered merge and the gradient table
+    "windows_48_16_d128": (lambda: synth.slanted_pair(288, 160, seed=83, d_max=110)[:2],
+                           dict(max_disparity=128, num_scales=3, num_paths=8,
+                                windows=(48, 16)), None),
+    "windows_20_8_ragged": (lambda: synth.bands_pair(203, 117, seed=84)[:2],
+                            dict(max_disparity=48, num_scales=3, num_paths=8, windows=(20, 8)),
+                            None),
+    "windows_s4_paper_grad": (lambda: synth.slanted_pair(256, 160, seed=85, d_max=100)[:2],
+                              dict(max_disparity=128, num_scales=4, num_paths=8,
+                                   windows=(0, 24, 12), merge_mode=PAPER), exp_table(10, 16)),
+    "full_windows_48_16_1280x720": (lambda: synth.slanted_pair(1280, 720, seed=0)[:2],
+                                    dict(max_disparity=128, num_scales=3, num_paths=8,
+                                         windows=(48, 16)), None),
+    # the benchmarked variants at their full size: 1280x720, D = 128, 3 scales (the
+    # 1280-step horizontal chains, the prefetch rings' wrap, every window shift)
+    "full_paper_1280x720_d128": (lambda: synth.slanted_pair(1280, 720, seed=0)[:2],
+                                 dict(max_disparity=128, num_scales=3, num_paths=8,
+                                      merge_mode=PAPER), None),
+    "full_grad_1280x720_d128": (lambda: synth.slanted_pair(1280, 720, seed=0)[:2],
+                                dict(max_disparity=128, num_scales=3, num_paths=8),
+                                exp_table(10, 16)),
+    "full_paper_grad_1280x720_d128": (lambda: synth.slanted_pair(1280, 720, seed=0)[:2],
+                                      dict(max_disparity=128, num_scales=3, num_paths=8,
+                                           merge_mode=PAPER), exp_table(10, 16)),
 }
 
 
