@@ -13,10 +13,20 @@ holds the device buffers.  Training labels are the plain pyramid matcher's own m
 Weight file (little endian): b"MPVP", version=1, layers, D, factor, then per layer
 (cin, cout, relu) as int32, then per layer the fp32 weights [cout][cin][3][3] and the
 fp32 biases [cout].
+
+Training checkpoint (little endian): b"MPVC", version=1, layers, D, factor as int32, then
+the Adam step, the generated pairs consumed, the samples seen and the next data seed as
+int64, the sampler's RNG state (int64 length, then bytes), per layer (cin, cout, relu) as
+int32, then per layer the fp32 weights, biases, and the Adam first and second moments of
+both; last, the CRC-32 (zlib) of every preceding byte as uint32.  A training run resumed
+from it continues the same data stream and optimizer; its replay buffer starts empty and
+refills from the next pairs.
 """
 from __future__ import annotations
 
+import os
 import struct
+import zlib
 
 import numpy as np
 
@@ -81,6 +91,68 @@ def load_weights(path):
     return layers, D, factor
 
 
+CKPT_MAGIC, CKPT_VERSION = b"MPVC", 1
+
+
+def save_checkpoint(path, state):
+    """state: dict(layers=[(w, b, relu)], adam=[(mw, vw, mb, vb)], step, pairs, samples,
+    next_seed, rng (bytes), D, factor).  Written to a temporary file and renamed, so a
+    crash mid-write leaves the previous checkpoint intact."""
+    parts = [CKPT_MAGIC, struct.pack("<4i", CKPT_VERSION, len(state["layers"]), state["D"],
+                                     state["factor"]),
+             struct.pack("<4q", state["step"], state["pairs"], state["samples"],
+                         state["next_seed"]),
+             struct.pack("<q", len(state["rng"])), bytes(state["rng"])]
+    for w, b, relu in state["layers"]:
+        parts.append(struct.pack("<3i", w.shape[1], w.shape[0], int(relu)))
+    for (w, b, _), (mw, vw, mb, vb) in zip(state["layers"], state["adam"]):
+        for a in (w, b, mw, vw, mb, vb):
+            parts.append(np.ascontiguousarray(a, np.float32).tobytes())
+    body = b"".join(parts)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "wb") as f:
+        f.write(body + struct.pack("<I", zlib.crc32(body) & 0xFFFFFFFF))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path):
+    """The state save_checkpoint wrote; ValueError on a wrong magic, version, size or CRC."""
+    with open(path, "rb") as f:
+        data = f.read()
+    if len(data) < 4 + 16 + 32 + 8 + 4 or data[:4] != CKPT_MAGIC:
+        raise ValueError("not a proposal training checkpoint")
+    body, (crc,) = data[:-4], struct.unpack("<I", data[-4:])
+    if zlib.crc32(body) & 0xFFFFFFFF != crc:
+        raise ValueError("checkpoint CRC mismatch (corrupt or truncated file)")
+    ver, n, D, factor = struct.unpack_from("<4i", body, 4)
+    if ver != CKPT_VERSION:
+        raise ValueError(f"checkpoint version {ver}, expected {CKPT_VERSION}")
+    step, pairs, samples, next_seed = struct.unpack_from("<4q", body, 20)
+    (nrng,) = struct.unpack_from("<q", body, 52)
+    off = 60
+    rng = body[off:off + nrng]
+    off += nrng
+    shapes = []
+    for _ in range(n):
+        shapes.append(struct.unpack_from("<3i", body, off))
+        off += 12
+    layers, adam = [], []
+    for cin, cout, relu in shapes:
+        arrs = []
+        for size, shape in ((cout * cin * 9, (cout, cin, 3, 3)), (cout, (cout,)),
+                            (cout * cin * 9, (cout, cin, 3, 3)), (cout * cin * 9, (cout, cin, 3, 3)),
+                            (cout, (cout,)), (cout, (cout,))):
+            arrs.append(np.frombuffer(body, np.float32, size, off).reshape(shape).copy())
+            off += 4 * size
+        w, b, mw, vw, mb, vb = arrs
+        layers.append((w, b, bool(relu)))
+        adam.append((mw, vw, mb, vb))
+    if off != len(body):
+        raise ValueError("checkpoint size does not match its header")
+    return dict(layers=layers, adam=adam, step=step, pairs=pairs, samples=samples,
+                next_seed=next_seed, rng=rng, D=D, factor=factor)
+
+
 class Net:
     """Device copies of the weights (fp32 master, bf16 working copy) and Adam state."""
 
@@ -101,6 +173,20 @@ class Net:
 
     def numpy_layers(self):
         return [(L["w"].cpu().numpy(), L["b"].cpu().numpy(), L["relu"]) for L in self.layers]
+
+    def adam_state(self):
+        return [tuple(L[k].cpu().numpy() for k in ("mw", "vw", "mb", "vb")) for L in self.layers]
+
+    @classmethod
+    def from_checkpoint(cls, state, device="cuda"):
+        """A network with the checkpoint's weights, Adam moments and step."""
+        net = cls(state["layers"], device)
+        torch = net.torch
+        for L, moments in zip(net.layers, state["adam"]):
+            for k, a in zip(("mw", "vw", "mb", "vb"), moments):
+                L[k].copy_(torch.from_numpy(np.ascontiguousarray(a)))
+        net.step = int(state["step"])
+        return net
 
     def forward(self, x_bf16):
         """x: [N, Cin, H, W] bf16 -> (prediction fp32 [N,1,H,W], stored activations)."""
@@ -222,7 +308,12 @@ class _Samples:
 
 
 def train(seconds=600.0, out="proposal.bin", capacity=4096, batch=8, steps_per_pair=4,
-          lr=1e-3, delta=1.0 / 128, seed0=10000, log=print):
+          lr=1e-3, delta=1.0 / 128, seed0=10000, log=print, checkpoint=None,
+          checkpoint_every=300.0, resume=None):
+    """Trains on generated pairs for `seconds`.  checkpoint: a path written every
+    checkpoint_every seconds and at the end; resume: a checkpoint to continue from (its
+    optimizer state, step, data position and sampler; the learning-rate schedule
+    continues from the elapsed fraction it implies)."""
     import multiprocessing as mp
     import os
     import time
@@ -232,14 +323,30 @@ def train(seconds=600.0, out="proposal.bin", capacity=4096, batch=8, steps_per_p
     smp = _Samples(torch)
     feats = torch.empty((capacity, smp.cin, smp.Hq, smp.Wq), dtype=torch.bfloat16, device="cuda")
     targets = torch.empty((capacity, 1, smp.Hq, smp.Wq), dtype=torch.float32, device="cuda")
-    net = Net(init_weights(smp.cin, seed=1))
     gen = torch.Generator(device="cpu").manual_seed(0)
     n = 0
     pairs = 0
+    seed_next = seed0
+    if resume:
+        st = load_checkpoint(resume)
+        net = Net.from_checkpoint(st)
+        n, pairs, seed_next = int(st["samples"]), int(st["pairs"]), int(st["next_seed"])
+        gen.set_state(torch.frombuffer(bytearray(st["rng"]), dtype=torch.uint8))
+        log(f"resumed at step {net.step}, {pairs} pairs, next seed {seed_next}")
+    else:
+        net = Net(init_weights(smp.cin, seed=1))
     t0 = time.perf_counter()
+    t_ckpt = t0
+
+    def write_ckpt():
+        save_checkpoint(checkpoint, dict(layers=net.numpy_layers(), adam=net.adam_state(),
+                                         step=net.step, pairs=pairs, samples=n,
+                                         next_seed=seed_next, rng=gen.get_state().numpy().tobytes(),
+                                         D=D_TRAIN, factor=1 << (S_TRAIN - 1)))
     losses = []
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
-        for _seed, L, R in pool.imap_unordered(_gen_pair, range(seed0, seed0 + 10**6), 4):
+        for _seed, L, R in pool.imap(_gen_pair, range(seed_next, seed_next + 10**6), 4):
+            seed_next = _seed + 1
             slot = n % capacity
             s2 = (slot + 1) % capacity
             smp.make(L, R, (feats[slot], feats[s2]), (targets[slot], targets[s2]))
@@ -256,10 +363,15 @@ def train(seconds=600.0, out="proposal.bin", capacity=4096, batch=8, steps_per_p
                 losses.append(float(loss.item()))
                 log(f"pairs {pairs} samples {n} loss {losses[-1]:.5f} "
                     f"t {time.perf_counter() - t0:.0f}s")
+            if checkpoint and time.perf_counter() - t_ckpt > checkpoint_every:
+                write_ckpt()
+                t_ckpt = time.perf_counter()
             if time.perf_counter() - t0 > seconds:
                 pool.terminate()
                 break
     smp.close()
+    if checkpoint:
+        write_ckpt()
     save_weights(out, net.numpy_layers(), D_TRAIN, 1 << (S_TRAIN - 1))
     return dict(pairs=pairs, samples=n, steps=net.step, losses=losses,
                 seconds=time.perf_counter() - t0)
@@ -362,10 +474,13 @@ def main():
     ap.add_argument("--eval-pairs", type=int, default=40)
     ap.add_argument("--eval-only", action="store_true")
     ap.add_argument("--report", default=None)
+    ap.add_argument("--checkpoint", default=None, help="write a training checkpoint here")
+    ap.add_argument("--resume", default=None, help="continue from this checkpoint")
     args = ap.parse_args()
     res = {}
     if not args.eval_only:
-        res["train"] = train(seconds=args.seconds, out=args.out)
+        res["train"] = train(seconds=args.seconds, out=args.out, checkpoint=args.checkpoint,
+                             resume=args.resume)
     res["eval"] = evaluate(args.out, npairs=args.eval_pairs)
     if args.report:
         with open(args.report, "w") as f:
