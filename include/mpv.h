@@ -228,8 +228,40 @@ mpv_status mpv_proposal_stats(const mpv_ctx *ctx, uint64_t *edge_hits, uint64_t 
  * it opened them.                                                                     */
 mpv_status mpv_proposal_fallbacks(const mpv_ctx *ctx, uint64_t *frames, uint64_t *fallbacks);
 
-/* Waits for the context's last submitted work and returns any latched device error. */
+/* Waits for the context's last submitted work and returns any latched device error,
+ * MPV_ERR_TIMEOUT among them: the last persistent batch ended by its bounded wait.     */
 mpv_status mpv_sync(mpv_ctx *ctx);
+
+/* Batches (mpv_match_batch with n > 1) run either through one persistent kernel over a
+ * device work list or as a CUDA graph of per-pair launch sequences over worker streams.
+ * The persistent kernel applies when every pair uses the summed merge with pyramid
+ * windows, no gradient table, no top-level tiles, a jump radius ceil(T/p1) - 1 <= 2 and
+ * label strides of 16, 32, 48 or 64 (and MPV_BATCH_STREAMS is not set in the
+ * environment).  Each pair's stages become work items in per-group queues; a kernel CTA
+ * claims an item only once the stage it depends on has completed, and the search for a
+ * claimable item is the one device-side wait, bounded in clock cycles (about 2 s): when
+ * it runs out the batch stops and mpv_sync returns MPV_ERR_TIMEOUT.  Once per set of
+ * pair shapes the autotuner times the persistent kernel with each candidate shape
+ * (lanes per scan path, work queues, cost blocks per item) and the stream graph on the
+ * batch itself, and keeps the fastest; all give the same bit-exact maps.
+ * mpv_batch_info reports the path of the context's last batch (persistent 1 or 0), the
+ * persistent shapes and the tuner's times in milliseconds per batch (0 when not tuned). */
+mpv_status mpv_batch_info(const mpv_ctx *ctx, int32_t *persistent, int32_t *lanes,
+                          int32_t *queues, int32_t *cost_blocks, float *persistent_ms,
+                          float *streams_ms);
+
+/* Which batch path mpv_match_batch takes: MPV_BATCH_AUTO (default: the autotuner's
+ * choice), MPV_BATCH_PERSISTENT (the persistent kernel wherever it applies) or
+ * MPV_BATCH_STREAMS (always the stream graph).                                          */
+#define MPV_BATCH_AUTO 0
+#define MPV_BATCH_PERSISTENT 1
+#define MPV_BATCH_STREAMS 2
+mpv_status mpv_set_batch_mode(mpv_ctx *ctx, int32_t mode);
+
+/* Test hook of the bounded wait: the next persistent batch makes one stage of its largest
+ * pair wait for an item that never exists and gives its wait wait_cycles clock cycles;
+ * that launch is not cached, and mpv_sync afterwards returns MPV_ERR_TIMEOUT.           */
+mpv_status mpv_debug_batch_stall(mpv_ctx *ctx, int64_t wait_cycles);
 
 /* Device bytes the context needs for a width x height pair at its parameters. */
 mpv_status mpv_workspace_bytes(const mpv_ctx *ctx, int32_t width, int32_t height,

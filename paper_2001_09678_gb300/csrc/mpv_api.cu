@@ -59,6 +59,24 @@ struct mpv_ctx {
     bool grad_on = false;
     int32_t grad_host[256] = {};
     int *grad_dev = nullptr;
+    // persistent batches: per signature the uploaded plan (device), its tuned shapes and
+    // graph; the status word of the last launch (pinned); the bounded wait in clock cycles
+    struct PBatch {
+        uint64_t sig;
+        void *dev;
+        cudaGraphExec_t exec;
+        BatchTune tune;
+    };
+    std::vector<PBatch> pbatches;
+    std::map<uint64_t, BatchTune> btuning;
+    int *bstatus_host = nullptr;
+    long long wait_cycles = 4000000000ll;   // about 2 s at the GPU's clock
+    bool stall_next = false;                // test hook (mpv_debug_batch_stall)
+    long long stall_wait_cycles = 0;
+    bool persistent = std::getenv("MPV_BATCH_STREAMS") == nullptr;
+    BatchTune last_batch;                   // the last batch's path and shapes
+    int *err_dev = nullptr;                 // bounds-checked builds: the device error word
+    int batch_mode = MPV_BATCH_AUTO;
     // road detection: steps back of the profile when they do not fit in shared memory
     void *road_scratch = nullptr;
     size_t road_scratch_bytes = 0;
@@ -192,8 +210,20 @@ mpv_status check_grad(const mpv_ctx *ctx)
     return MPV_OK;
 }
 
+void drop_pbatches(mpv_ctx *ctx)
+{
+    if (ctx->pbatches.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto &b : ctx->pbatches) {
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        if (b.dev) cudaFree(b.dev);
+    }
+    ctx->pbatches.clear();
+}
+
 void drop_graphs(mpv_ctx *ctx)
 {
+    drop_pbatches(ctx);
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
     for (auto &g : ctx->singles) cudaGraphExecDestroy(g.exec);
@@ -230,6 +260,7 @@ mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
     for (int c : cands) {
         Tuning t;
         t.lanes = c;
+        t.err = ctx->err_dev;
         enqueue_pair(ctx->p, job, (uint8_t *)ctx->ws, s, nullptr, nullptr, t, &ctx->net,
                      ctx->lut());
         float tot = 0.f;
@@ -257,11 +288,194 @@ mpv_status autotune(mpv_ctx *ctx, const PairJob &job, Tuning &out)
     return MPV_OK;
 }
 
+mpv_status run_batch_streams(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stream);
+
+// The batch through one persistent kernel over a device work list (batch.cu): every pair
+// gets its own workspace region; the plan is uploaded once per batch signature and its
+// launch (state clear, kernel, status copy) captured as a CUDA graph that repeats replay.
+// The launch shapes come from the batch autotuner, which times each candidate on the
+// batch itself and keeps the fastest (all give the same bit-exact maps).
+mpv_status run_batch_persistent(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stream)
+{
+    mpv_status st = ensure_batch_streams(ctx);
+    if (st != MPV_OK) return st;
+    if (!ctx->bstatus_host) {
+        if (cudaMallocHost(&ctx->bstatus_host, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return MPV_ERR_OOM;
+        }
+        *ctx->bstatus_host = 0;
+    }
+    std::vector<size_t> off(n);
+    size_t total = 0;
+    uint64_t shapes = 0;
+    for (int i = 0; i < n; ++i) {
+        off[i] = total;
+        total += (batch_pair_bytes(ctx->p, jobs[i]) + 255) & ~(size_t)255;
+        shapes = mix64(shapes, shape_key(ctx->p, jobs[i].W, jobs[i].H, jobs[i].D));
+    }
+    if (total > ctx->bws_bytes) {
+        if (ctx->ws_limit && total > ctx->ws_limit) return MPV_ERR_OOM;
+        drop_graphs(ctx);
+        if (ctx->bws) {
+            cudaDeviceSynchronize();
+            cudaFree(ctx->bws);
+            ctx->bws = nullptr;
+            ctx->bws_bytes = 0;
+        }
+        const cudaError_t e = cudaMalloc(&ctx->bws, total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+        ctx->bws_bytes = total;
+    }
+    uint64_t sig = mix64(shapes, (uint64_t)(uintptr_t)ctx->bws);
+    for (int i = 0; i < n; ++i) {
+        const PairJob &j = jobs[i];
+        sig = mix64(sig, (uint64_t)(uintptr_t)j.left);
+        sig = mix64(sig, (uint64_t)(uintptr_t)j.right);
+        sig = mix64(sig, (uint64_t)(uintptr_t)j.disp);
+        sig = mix64(sig, (uint64_t)(uintptr_t)j.disp_right);
+        sig = mix64(sig, ((uint64_t)j.pitch << 32) | (uint32_t)j.disp_pitch);
+    }
+    const bool stall = ctx->stall_next;
+    ctx->stall_next = false;
+    if (!stall)
+        for (auto &b : ctx->pbatches)
+            if (b.sig == sig && ctx->batch_mode != MPV_BATCH_STREAMS &&
+                (b.tune.persistent || ctx->batch_mode == MPV_BATCH_PERSISTENT)) {
+                ctx->last_batch = b.tune;
+                ctx->last_batch.persistent = true;
+                return cuda_status(cudaGraphLaunch(b.exec, stream));
+            }
+
+    auto build = [&](const BatchTune &t0, void **dev, BatchDevice &bd) -> mpv_status {
+        BatchTune t = t0;
+        t.err = ctx->err_dev;
+        BatchPlan plan;
+        mpv_status r = plan_batch(ctx->p, jobs, n, (uint8_t *)ctx->bws, off.data(), t, plan);
+        if (r != MPV_OK) return r;
+        const cudaError_t e = cudaMalloc(dev, batch_device_bytes(plan));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+        return upload_batch(plan, *dev, bd);
+    };
+
+    // the launch shapes: tuned once per set of pair shapes
+    BatchTune tune;
+    auto tit = ctx->btuning.find(shapes);
+    if (tit != ctx->btuning.end()) {
+        tune = tit->second;
+    } else {
+        cudaStreamSynchronize(stream);
+        cudaStream_t s = ctx->workers[0];
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (int lanes : {8, 4})
+            for (int queues : {16, 32})
+                for (int cb : {2, 8}) {
+                    BatchTune t;
+                    t.lanes = lanes;
+                    t.queues = queues;
+                    t.cost_blocks = cb;
+                    void *dev = nullptr;
+                    BatchDevice bd;
+                    mpv_status r = build(t, &dev, bd);
+                    float ms = 1e30f;
+                    if (r == MPV_OK) {
+                        r = launch_batch(bd, ctx->wait_cycles, ctx->bstatus_host, s);   // warm
+                        cudaEventRecord(e0, s);
+                        if (r == MPV_OK) r = launch_batch(bd, ctx->wait_cycles, ctx->bstatus_host, s);
+                        cudaEventRecord(e1, s);
+                        cudaEventSynchronize(e1);
+                        if (r == MPV_OK && *ctx->bstatus_host == MPV_OK)
+                            cudaEventElapsedTime(&ms, e0, e1);
+                    }
+                    if (dev) cudaFree(dev);
+                    if (r != MPV_OK) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return r;
+                    }
+                    if (ms < best) {
+                        best = ms;
+                        tune = t;
+                    }
+                }
+        // the same batch as a graph of per-pair launch sequences over worker streams
+        float streams_ms = 1e30f;
+        {
+            mpv_status r = run_batch_streams(ctx, jobs, n, s);   // captures its graph
+            cudaEventRecord(e0, s);
+            if (r == MPV_OK) r = run_batch_streams(ctx, jobs, n, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            if (r == MPV_OK) cudaEventElapsedTime(&streams_ms, e0, e1);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *ctx->bstatus_host = 0;
+        tune.persistent = best <= streams_ms;
+        tune.ms = best;
+        tune.streams_ms = streams_ms;
+        ctx->btuning[shapes] = tune;
+    }
+    ctx->last_batch = tune;
+    ctx->last_batch.persistent = ctx->batch_mode == MPV_BATCH_PERSISTENT ||
+                                 (ctx->batch_mode == MPV_BATCH_AUTO && tune.persistent) || stall;
+    if (!ctx->last_batch.persistent) return run_batch_streams(ctx, jobs, n, stream);
+    BatchTune t = tune;
+    t.stall = stall;
+    void *dev = nullptr;
+    BatchDevice bd;
+    st = build(t, &dev, bd);
+    if (st != MPV_OK) {
+        if (dev) cudaFree(dev);
+        return st;
+    }
+    if (stall) {   // a one-off launch with the test hook: not cached
+        const mpv_status r = launch_batch(bd, ctx->stall_wait_cycles, ctx->bstatus_host, stream);
+        cudaStreamSynchronize(stream);
+        cudaFree(dev);
+        return r;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dev);
+        return MPV_ERR_CUDA;
+    }
+    const mpv_status lr = launch_batch(bd, ctx->wait_cycles, ctx->bstatus_host, ctx->cap);
+    e = cudaStreamEndCapture(ctx->cap, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && lr == MPV_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || lr != MPV_OK) {
+        cudaGetLastError();
+        cudaFree(dev);
+        return lr != MPV_OK ? lr : MPV_ERR_CUDA;
+    }
+    if (ctx->pbatches.size() >= 4) {   // keep a few signatures
+        cudaDeviceSynchronize();
+        cudaGraphExecDestroy(ctx->pbatches.front().exec);
+        cudaFree(ctx->pbatches.front().dev);
+        ctx->pbatches.erase(ctx->pbatches.begin());
+    }
+    ctx->pbatches.push_back({sig, dev, exec, tune});
+    return cuda_status(cudaGraphLaunch(exec, stream));
+}
+
 // Runs a batch as one CUDA graph: pair i runs on worker stream w(i) (largest pairs
 // first, round robin), pairs sharing a worker run one after another and share that
 // worker's workspace region, and the workers run concurrently.  The instantiated graph
 // is cached by the batch signature and replayed by a single graph launch.
-mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stream)
+mpv_status run_batch_streams(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stream)
 {
     if (check_grad(ctx) != MPV_OK) return MPV_ERR_INVALID_ARG;
     mpv_status st = ensure_batch_streams(ctx);
@@ -270,6 +484,7 @@ mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stre
     for (int i = 0; i < n; ++i) {
         st = autotune(ctx, jobs[i], tune[i]);
         if (st != MPV_OK) return st;
+        tune[i].err = ctx->err_dev;
     }
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
@@ -404,6 +619,7 @@ mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const Stage
     Tuning t;
     const auto it = ctx->tuning.find(shape_key(ctx->p, job.W, job.H, job.D));
     if (it != ctx->tuning.end()) t = it->second;
+    t.err = ctx->err_dev;
     const bool learned = ctx->p.proposal == MPV_PROPOSAL_LEARNED;
     if (learned && !ctx->net.layers) return MPV_ERR_INVALID_ARG;    // no weights loaded
     if (learned && !dbg && !ctx->edge_host) {
@@ -487,6 +703,22 @@ struct DeviceGuard {
     }
 };
 
+// A batch: through the persistent kernel where it applies and the autotuner found it
+// faster than the graph of worker streams, else through that graph.
+mpv_status run_batch(mpv_ctx *ctx, const PairJob *jobs, int n, cudaStream_t stream)
+{
+    if (check_grad(ctx) != MPV_OK) return MPV_ERR_INVALID_ARG;
+    if (ctx->persistent && !ctx->grad_on && ctx->batch_mode != MPV_BATCH_STREAMS) {
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i)
+            ok = batch_supported(ctx->p, jobs[i].W, jobs[i].H, jobs[i].D);
+        if (ok) return run_batch_persistent(ctx, jobs, n, stream);
+    }
+    ctx->last_batch = BatchTune();
+    ctx->last_batch.persistent = false;
+    return run_batch_streams(ctx, jobs, n, stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -527,6 +759,17 @@ mpv_status mpv_create(int device, mpv_ctx **out)
     if (!c) return MPV_ERR_OOM;
     c->device = device;
     mpv_default_params(&c->p);
+#ifdef MPV_DEBUG_BOUNDS
+    {
+        DeviceGuard guard(device);
+        if (cudaMalloc(&c->err_dev, sizeof(int)) != cudaSuccess ||
+            cudaMemset(c->err_dev, 0, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return MPV_ERR_OOM;
+        }
+    }
+#endif
     *out = c;
     return MPV_OK;
 }
@@ -855,9 +1098,52 @@ mpv_status mpv_sync(mpv_ctx *ctx)
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
+    if (ctx->err_dev) {   // bounds-checked builds: a device index check failed
+        int site = 0;
+        cudaMemcpy(&site, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+        if (site) {
+            std::fprintf(stderr, "mpv: device bounds check failed at site %d\n", site);
+            cudaMemset(ctx->err_dev, 0, sizeof(int));
+            ctx->latched = MPV_ERR_INTERNAL;
+        }
+    }
+    if (ctx->bstatus_host && *ctx->bstatus_host != MPV_OK) {   // a persistent batch's wait ran out
+        ctx->latched = *ctx->bstatus_host;
+        *ctx->bstatus_host = MPV_OK;
+    }
     const mpv_status st = (mpv_status)ctx->latched;
     ctx->latched = MPV_OK;
     return st;
+}
+
+mpv_status mpv_set_batch_mode(mpv_ctx *ctx, int32_t mode)
+{
+    if (!ctx || mode < MPV_BATCH_AUTO || mode > MPV_BATCH_STREAMS) return MPV_ERR_INVALID_ARG;
+    ctx->batch_mode = mode;
+    return MPV_OK;
+}
+
+mpv_status mpv_debug_batch_stall(mpv_ctx *ctx, int64_t wait_cycles)
+{
+    if (!ctx || wait_cycles < 1) return MPV_ERR_INVALID_ARG;
+    ctx->stall_next = true;
+    ctx->stall_wait_cycles = wait_cycles;
+    return MPV_OK;
+}
+
+mpv_status mpv_batch_info(const mpv_ctx *ctx, int32_t *persistent, int32_t *lanes,
+                          int32_t *queues, int32_t *cost_blocks, float *persistent_ms,
+                          float *streams_ms)
+{
+    if (!ctx) return MPV_ERR_INVALID_ARG;
+    const BatchTune &t = ctx->last_batch;
+    if (persistent) *persistent = t.persistent ? 1 : 0;
+    if (lanes) *lanes = t.lanes;
+    if (queues) *queues = t.queues;
+    if (cost_blocks) *cost_blocks = t.cost_blocks;
+    if (persistent_ms) *persistent_ms = t.ms;
+    if (streams_ms) *streams_ms = t.streams_ms;
+    return MPV_OK;
 }
 
 mpv_status mpv_workspace_bytes(const mpv_ctx *ctx, int32_t width, int32_t height, size_t *bytes)
@@ -1011,6 +1297,9 @@ void mpv_destroy(mpv_ctx *ctx)
         if (ctx->net_mem) cudaFree(ctx->net_mem);
         if (ctx->grad_dev) cudaFree(ctx->grad_dev);
         if (ctx->road_scratch) cudaFree(ctx->road_scratch);
+        drop_pbatches(ctx);
+        if (ctx->err_dev) cudaFree(ctx->err_dev);
+        if (ctx->bstatus_host) cudaFreeHost(ctx->bstatus_host);
         if (ctx->edge_host) cudaFreeHost(ctx->edge_host);
         if (ctx->counters_dev) cudaFree(ctx->counters_dev);
     }

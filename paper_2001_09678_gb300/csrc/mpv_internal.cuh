@@ -19,6 +19,28 @@ constexpr int kInf = 1 << 28;
 // still below 2^16 after adding any penalty term (< 16384).
 constexpr uint32_t kInf16 = 0x4000u;
 
+// Bounds-checked builds (compiled with MPV_DEBUG_BOUNDS): MPV_IN(err, ok, site) is false
+// when an index check fails, after recording the first failing site in the device error
+// word err (the caller then skips the access); mpv_sync reports MPV_ERR_INTERNAL.  In
+// the normal build it is the constant true and the checks vanish.
+#ifdef MPV_DEBUG_BOUNDS
+__device__ __forceinline__ bool mpv_in(int *err, bool ok, int site)
+{
+    if (!ok && err) atomicCAS(err, 0, site);
+    return ok;
+}
+#define MPV_IN(err, ok, site) mpv_in((err), (ok), (site))
+#else
+#define MPV_IN(err, ok, site) true
+#endif
+
+// floor((a + b) / 2) of each 16-bit half: a & b + ((a ^ b) >> 1), the shift masked so
+// that no bit crosses from the high half into the low half
+__device__ __forceinline__ uint32_t avg_u16x2(uint32_t a, uint32_t b)
+{
+    return (a & b) + (((a ^ b) >> 1) & 0x7FFF7FFFu);
+}
+
 // Buffers of one view at one pyramid level.  View 0 is the left view (I0 = left,
 // I1 = right); view 1 is the matcher run on the mirrored, swapped pair.
 struct ViewLevel {
@@ -53,11 +75,13 @@ struct LevelArgs {
     int block_cut;   // > 0: independent block_cut x block_cut tiles (scan paths restart)
     int zero_s;      // the cost kernel also clears S (the summed merge accumulates into it)
     const int *gate; // optional device word: 0 = every kernel of this level returns at once
+    int *err;        // bounds-checked builds: the device error word (see MPV_IN)
 };
 
 // Launch shapes chosen per image shape by the autotuner.
 struct Tuning {
     int lanes = 8;   // aggregation: lanes per scan path (4 or 8)
+    int *err = nullptr;   // bounds-checked builds: the context's device error word
 };
 
 struct SeedArgs {
@@ -67,6 +91,7 @@ struct SeedArgs {
     const uint16_t *dprev[kMaxViews];
     uint16_t *lo[kMaxViews];
     const int *gate;   // as LevelArgs::gate
+    int *err;          // as LevelArgs::err
 };
 
 struct ImageJob {       // one 2x2 down-sampling or mirror job
@@ -177,6 +202,9 @@ struct Layout {
     size_t img0[kMaxViews][kMaxScales], img1[kMaxViews][kMaxScales];
     size_t lo[kMaxViews][kMaxScales], d[kMaxViews][kMaxScales];
     size_t C[kMaxViews], S[kMaxViews];
+    // cost and summed volumes used at each level: C[v] and S[v] for every level, or with
+    // level_volumes one pair per level (no address reused within a launch)
+    size_t Cl[kMaxViews][kMaxScales] = {}, Sl[kMaxViews][kMaxScales] = {};
     size_t X[kMaxViews][3] = {};                  // layered merge: three more volumes per view
     size_t feat = 0, act0 = 0, act1 = 0, q = 0;   // learned proposal (both views)
     size_t edge = 0;                              // edge-hit counters
@@ -223,10 +251,33 @@ struct StageSink {
 bool params_valid(const mpv_params &p);
 mpv_status validate_pair(const mpv_params &p, int W, int H, int pitch, int disp_pitch, int D);
 void make_geometry(const mpv_params &p, int W, int H, int D, Geometry &g);
-Layout make_layout(const Geometry &g, int nviews, const mpv_params &p);
+Layout make_layout(const Geometry &g, int nviews, const mpv_params &p, bool level_volumes = false);
 // Window width of the finest level under the learned proposal (centre +- 8 by default).
 int learned_window(const mpv_params &p, int D);
 int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg);
+
+// Buffers and pyramid jobs of one pair in its workspace, shared by the launch sequence
+// (enqueue_pair) and the batch scheduler.
+struct PairPlan {
+    Geometry g;
+    Layout L;
+    int nviews = 1;
+    const uint8_t *I0[kMaxViews][kMaxScales] = {}, *I1[kMaxViews][kMaxScales] = {};
+    int P0[kMaxViews][kMaxScales] = {}, P1[kMaxViews][kMaxScales] = {};
+    ImageJob mirror[2];      // one scale with the right view: its mirrored full-size pair
+    int nmirror = 0;
+    PyrJob pyr[4];           // the two levels below the input, all images
+    int npyr = 0;
+    ImageJob down[kMaxScales][4];   // level l from level l+1, for l <= top - 3
+    int ndown[kMaxScales] = {};
+};
+void plan_pair(const mpv_params &p, const PairJob &job, uint8_t *base, int nviews,
+               bool level_volumes, PairPlan &pp);
+// Arguments of level l (both views) and of its window seeding (l > 0).
+LevelArgs level_args(const mpv_params &p, const PairPlan &pp, uint8_t *base, int l,
+                     const Tuning &tune, const int *gate);
+SeedArgs seed_args(const PairPlan &pp, uint8_t *base, int l, const int *gate,
+                   int *err = nullptr);
 
 // Enqueues the whole matcher for one pair on stream s, with its scratch at `workspace`
 // (at least make_layout(...).total bytes).
@@ -241,6 +292,52 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *worksp
                         const int *gate = nullptr, cudaStream_t aux = nullptr);
 // The context's loaded proposal network fits a range of D labels.
 bool proposal_fits(const mpv_ctx *ctx, int D);
+
+// ---- batches through one persistent kernel (batch.cu) -------------------------------
+
+// Launch shapes of a persistent batch, chosen by the batch autotuner.
+struct BatchTune {
+    int lanes = 8;         // lanes per scan path of the 32-label passes (8 or 4)
+    int queues = 16;       // work queues (groups of pairs, like streams)
+    int cost_blocks = 4;   // cost-kernel blocks per work item
+    bool stall = false;    // test hook: one stage never completes (bounded-wait test)
+    int *err = nullptr;    // bounds-checked builds: the device error word
+    // the tuner's verdict: the persistent kernel was faster than the stream graph, with
+    // the times it measured (ms per batch)
+    bool persistent = true;
+    float ms = 0.f, streams_ms = 0.f;
+};
+
+// Device addresses of an uploaded plan.
+struct BatchDevice {
+    void *pairs = nullptr, *items = nullptr, *queues = nullptr, *totals = nullptr;
+    void *state = nullptr;   // cleared before every launch: status, abort, heads, counters
+    size_t state_bytes = 0, smem = 0;
+    int nqueues = 0, nitems = 0;
+};
+
+class BatchPlan {
+public:
+    BatchPlan();
+    ~BatchPlan();
+    BatchPlan(const BatchPlan &) = delete;
+    BatchPlan &operator=(const BatchPlan &) = delete;
+    struct Impl;
+    Impl *impl;
+};
+
+// The persistent path handles the summed merge with pyramid windows, radius <= 2 and
+// label strides of 16, 32, 48 or 64 (else the batch runs as a graph of streams).
+bool batch_supported(const mpv_params &p, int W, int H, int D);
+// Workspace of one pair on the persistent path (a volume pair per level).
+size_t batch_pair_bytes(const mpv_params &p, const PairJob &job);
+mpv_status plan_batch(const mpv_params &p, const PairJob *jobs, int n, uint8_t *base,
+                      const size_t *offsets, const BatchTune &tune, BatchPlan &plan);
+size_t batch_device_bytes(const BatchPlan &plan);
+mpv_status upload_batch(const BatchPlan &plan, void *dev, BatchDevice &out);
+// Clears the state, runs the persistent kernel, copies the status word to status_host.
+mpv_status launch_batch(const BatchDevice &bd, long long wait_cycles, int *status_host,
+                        cudaStream_t s);
 
 // Network input of the top level of `view` (2 + D_top channels, BF16) into out.
 mpv_status enqueue_features(const mpv_params &p, const PairJob &job, uint8_t *workspace,

@@ -123,7 +123,7 @@ int learned_window(const mpv_params &p, int D)
     return w < D ? w : D;
 }
 
-Layout make_layout(const Geometry &g, int nviews, const mpv_params &p)
+Layout make_layout(const Geometry &g, int nviews, const mpv_params &p, bool level_volumes)
 {
     const bool learned = p.proposal == MPV_PROPOSAL_LEARNED;
     const bool layered = p.merge_mode == MPV_MERGE_PAPER;
@@ -145,6 +145,21 @@ Layout make_layout(const Geometry &g, int nviews, const mpv_params &p)
         }
         L.C[v] = take(off, sizeof(uint8_t) * (size_t)maxvol);
         L.S[v] = take(off, sizeof(uint16_t) * (size_t)maxvol);
+        for (int l = 0; l < g.S; ++l) {
+            L.Cl[v][l] = L.C[v];
+            L.Sl[v][l] = L.S[v];
+        }
+        if (level_volumes) {   // one level keeps C[v], S[v]; every other has its own pair
+            int big = 0;
+            for (int l = 0; l < g.S; ++l)
+                if ((int64_t)g.W[l] * g.H[l] * g.Dws[l] == maxvol) big = l;
+            for (int l = 0; l < g.S; ++l) {
+                if (l == big) continue;
+                const size_t vol = (size_t)g.W[l] * g.H[l] * g.Dws[l];
+                L.Cl[v][l] = take(off, sizeof(uint8_t) * vol);
+                L.Sl[v][l] = take(off, sizeof(uint16_t) * vol);
+            }
+        }
         if (layered)
             for (int i = 0; i < 3; ++i) L.X[v][i] = take(off, sizeof(uint16_t) * (size_t)maxvol);
     }
@@ -191,7 +206,7 @@ mpv_status enqueue_features(const mpv_params &p, const PairJob &job, uint8_t *ba
     const uint8_t *I0 = (view == 0 && top == 0) ? job.left : base + L.img0[view][0];
     const uint8_t *I1 = (view == 0 && top == 0) ? job.right : base + L.img1[view][0];
     const int pitch = (view == 0 && top == 0) ? job.pitch : g.pitch[0];
-    launch_features(I0, pitch, I1, pitch, base + L.C[view], g.Dws[0], g.Dw[0], g.W[0], g.H[0],
+    launch_features(I0, pitch, I1, pitch, base + L.Cl[view][0], g.Dws[0], g.Dw[0], g.W[0], g.H[0],
                     out, s);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPV_OK : MPV_ERR_CUDA;
@@ -200,6 +215,126 @@ mpv_status enqueue_features(const mpv_params &p, const PairJob &job, uint8_t *ba
 int views_needed(const mpv_params &p, const PairJob &job, const StageSink *dbg)
 {
     return (p.lr_check || job.disp_right || (dbg && dbg->view == 1)) ? 2 : 1;
+}
+
+void plan_pair(const mpv_params &p, const PairJob &job, uint8_t *base, int nviews,
+               bool level_volumes, PairPlan &pp)
+{
+    make_geometry(p, job.W, job.H, job.D, pp.g);
+    pp.L = make_layout(pp.g, nviews, p, level_volumes);
+    pp.nviews = nviews;
+    const Geometry &g = pp.g;
+    const Layout &L = pp.L;
+    const int top = g.S - 1;
+    for (int v = 0; v < nviews; ++v)
+        for (int l = 0; l < g.S; ++l) {
+            pp.I0[v][l] = base + L.img0[v][l];
+            pp.I1[v][l] = base + L.img1[v][l];
+            pp.P0[v][l] = pp.P1[v][l] = g.pitch[l];
+        }
+    pp.I0[0][top] = job.left;
+    pp.I1[0][top] = job.right;
+    pp.P0[0][top] = pp.P1[0][top] = job.pitch;
+    // right view: the mirrored, swapped pair.  The first two levels below the input come
+    // from one launch that also writes the mirrored inputs; further levels one by one.
+    pp.nmirror = 0;
+    if (top == 0 && nviews == 2) {
+        pp.mirror[0] = {job.right, job.pitch, base + L.img0[1][top], g.pitch[top]};
+        pp.mirror[1] = {job.left, job.pitch, base + L.img1[1][top], g.pitch[top]};
+        pp.nmirror = 2;
+    }
+    pp.npyr = 0;
+    if (top >= 1) {
+        const int l1 = top - 1, l2 = top - 2;
+        for (int v = 0; v < nviews; ++v)
+            for (int k = 0; k < 2; ++k) {
+                // view 0: (left, right); view 1: (mirrored right, mirrored left)
+                const uint8_t *src = (v == 0) == (k == 0) ? job.left : job.right;
+                const size_t *dimg = k == 0 ? L.img0[v] : L.img1[v];
+                PyrJob &j = pp.pyr[pp.npyr++];
+                j.src = src;
+                j.src_pitch = job.pitch;
+                j.mirror = v;
+                j.full = v ? base + dimg[top] : nullptr;
+                j.full_pitch = g.pitch[top];
+                j.d1 = base + dimg[l1];
+                j.p1 = g.pitch[l1];
+                j.d2 = l2 >= 0 ? base + dimg[l2] : nullptr;
+                j.p2 = l2 >= 0 ? g.pitch[l2] : 0;
+            }
+    }
+    for (int l = 0; l < kMaxScales; ++l) pp.ndown[l] = 0;
+    for (int l = top - 3; l >= 0; --l) {
+        int n = 0;
+        for (int v = 0; v < nviews; ++v) {
+            pp.down[l][n++] = {pp.I0[v][l + 1], pp.P0[v][l + 1], base + L.img0[v][l], g.pitch[l]};
+            pp.down[l][n++] = {pp.I1[v][l + 1], pp.P1[v][l + 1], base + L.img1[v][l], g.pitch[l]};
+        }
+        pp.ndown[l] = n;
+    }
+}
+
+LevelArgs level_args(const mpv_params &p, const PairPlan &pp, uint8_t *base, int l,
+                     const Tuning &tune, const int *gate)
+{
+    const Geometry &g = pp.g;
+    const Layout &L = pp.L;
+    LevelArgs a{};
+    a.W = g.W[l];
+    a.H = g.H[l];
+    a.D = g.D[l];
+    a.Dw = g.Dw[l];
+    a.Dws = g.Dws[l];
+    a.nviews = pp.nviews;
+    a.N = p.ssim_window;
+    a.c1 = ssim_c1(a.N);
+    a.c2 = ssim_c2(a.N);
+    // penalty min(p1 |du|, T) over labels of one level: |du| <= D_l - 1, so a
+    // truncation above p1 (D_l - 1) never acts and p1 above T acts as T
+    const int64_t span = (int64_t)p.p1 * (g.D[l] - 1);
+    const int64_t Teff = (int64_t)p.trunc < span ? p.trunc : span;
+    a.trunc = (int)Teff;
+    a.p1 = (int)(p.p1 < Teff ? p.p1 : Teff);
+    a.radius = a.p1 > 0 ? (int)((Teff + a.p1 - 1) / a.p1) - 1 : 0;
+    a.npaths = p.num_paths;
+    a.lanes = tune.lanes;
+    a.block_cut = l == 0 ? p.top_block : 0;
+    a.gate = gate;
+    a.err = tune.err;
+    for (int v = 0; v < pp.nviews; ++v) {
+        ViewLevel &vl = a.v[v];
+        vl.I0 = pp.I0[v][l];
+        vl.I1 = pp.I1[v][l];
+        vl.pitch0 = pp.P0[v][l];
+        vl.pitch1 = pp.P1[v][l];
+        vl.lo = l == 0 ? nullptr : (const uint16_t *)(base + L.lo[v][l]);
+        vl.C = base + L.Cl[v][l];
+        vl.S = (uint16_t *)(base + L.Sl[v][l]);
+        vl.d = (uint16_t *)(base + L.d[v][l]);
+        vl.S2 = nullptr;
+    }
+    return a;
+}
+
+SeedArgs seed_args(const PairPlan &pp, uint8_t *base, int l, const int *gate, int *err)
+{
+    const Geometry &g = pp.g;
+    SeedArgs sa{};
+    sa.W = g.W[l];
+    sa.H = g.H[l];
+    sa.Wp = g.W[l - 1];
+    sa.Hp = g.H[l - 1];
+    sa.block = g.block[l];
+    sa.Dw = g.Dw[l];
+    sa.D = g.D[l];
+    sa.nviews = pp.nviews;
+    sa.gate = gate;
+    sa.err = err;
+    for (int v = 0; v < pp.nviews; ++v) {
+        sa.dprev[v] = (const uint16_t *)(base + pp.L.d[v][l - 1]);
+        sa.lo[v] = (uint16_t *)(base + pp.L.lo[v][l]);
+    }
+    return sa;
 }
 
 namespace {
@@ -265,104 +400,31 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
             return MPV_ERR_INVALID_ARG;
         if (dbg && dbg->level != 0 && dbg->level != g.S - 1) return MPV_ERR_INVALID_ARG;
     }
-    const Layout L = make_layout(g, nviews, p);
+    PairPlan pp;
+    plan_pair(p, job, base, nviews, false, pp);
+    const Layout &L = pp.L;
     const bool layered = p.merge_mode == MPV_MERGE_PAPER;
     unsigned long long *edge = (unsigned long long *)(base + L.edge);
     const int S = g.S;
     const int top = S - 1;
-
-    const uint8_t *I0[kMaxViews][kMaxScales];
-    const uint8_t *I1[kMaxViews][kMaxScales];
-    int P0[kMaxViews][kMaxScales], P1[kMaxViews][kMaxScales];
-    for (int v = 0; v < nviews; ++v)
-        for (int l = 0; l < S; ++l) {
-            I0[v][l] = base + L.img0[v][l];
-            I1[v][l] = base + L.img1[v][l];
-            P0[v][l] = P1[v][l] = g.pitch[l];
-        }
-    I0[0][top] = job.left;
-    I1[0][top] = job.right;
-    P0[0][top] = P1[0][top] = job.pitch;
-
-    // right view: the mirrored, swapped pair.  The first two levels below the input come
-    // from one launch that also writes the mirrored inputs; further levels one by one.
-    if (top == 0 && nviews == 2) {
+    if (pp.nmirror) {
         HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
-        ImageJob m[2] = {{job.right, job.pitch, base + L.img0[1][top], g.pitch[top]},
-                         {job.left, job.pitch, base + L.img1[1][top], g.pitch[top]}};
-        launch_mirror(m, 2, job.W, job.H, s, gate);
+        launch_mirror(pp.mirror, pp.nmirror, job.W, job.H, s, gate);
     }
-    if (top >= 1) {
+    if (pp.npyr) {
         HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
-        const int l1 = top - 1, l2 = top - 2;
-        PyrJob pj[4];
-        int n = 0;
-        for (int v = 0; v < nviews; ++v)
-            for (int k = 0; k < 2; ++k) {
-                // view 0: (left, right); view 1: (mirrored right, mirrored left)
-                const uint8_t *src = (v == 0) == (k == 0) ? job.left : job.right;
-                const size_t *dimg = k == 0 ? L.img0[v] : L.img1[v];
-                PyrJob &j = pj[n++];
-                j.src = src;
-                j.src_pitch = job.pitch;
-                j.mirror = v;
-                j.full = v ? base + dimg[top] : nullptr;
-                j.full_pitch = g.pitch[top];
-                j.d1 = base + dimg[l1];
-                j.p1 = g.pitch[l1];
-                j.d2 = l2 >= 0 ? base + dimg[l2] : nullptr;
-                j.p2 = l2 >= 0 ? g.pitch[l2] : 0;
-            }
-        launch_pyramid2(pj, n, job.W, job.H, s, gate);
+        launch_pyramid2(pp.pyr, pp.npyr, job.W, job.H, s, gate);
     }
     for (int l = top - 3; l >= 0; --l) {
         HookScope hs(hook, MPV_STAGE_PYRAMID, 1, s);
-        ImageJob jobs[4];
-        int n = 0;
-        for (int v = 0; v < nviews; ++v) {
-            jobs[n++] = {I0[v][l + 1], P0[v][l + 1], base + L.img0[v][l], g.pitch[l]};
-            jobs[n++] = {I1[v][l + 1], P1[v][l + 1], base + L.img1[v][l], g.pitch[l]};
-        }
-        launch_down2(jobs, n, g.W[l + 1], g.H[l + 1], s, gate);
+        launch_down2(pp.down[l], pp.ndown[l], g.W[l + 1], g.H[l + 1], s, gate);
     }
 
     const int last = dbg ? dbg->level : top;
     if (!dbg && learned) cudaMemsetAsync(edge, 0, 2 * sizeof(unsigned long long), s);
     for (int l = 0; l <= last; ++l) {
         if (learned && l > 0 && l < top) continue;
-        LevelArgs a{};
-        a.W = g.W[l];
-        a.H = g.H[l];
-        a.D = g.D[l];
-        a.Dw = g.Dw[l];
-        a.Dws = g.Dws[l];
-        a.nviews = nviews;
-        a.N = p.ssim_window;
-        a.c1 = ssim_c1(a.N);
-        a.c2 = ssim_c2(a.N);
-        // penalty min(p1 |du|, T) over labels of one level: |du| <= D_l - 1, so a
-        // truncation above p1 (D_l - 1) never acts and p1 above T acts as T
-        const int64_t span = (int64_t)p.p1 * (g.D[l] - 1);
-        const int64_t Teff = (int64_t)p.trunc < span ? p.trunc : span;
-        a.trunc = (int)Teff;
-        a.p1 = (int)(p.p1 < Teff ? p.p1 : Teff);
-        a.radius = a.p1 > 0 ? (int)((Teff + a.p1 - 1) / a.p1) - 1 : 0;
-        a.npaths = p.num_paths;
-        a.lanes = tune.lanes;
-        a.block_cut = l == 0 ? p.top_block : 0;
-        a.gate = gate;
-        for (int v = 0; v < nviews; ++v) {
-            ViewLevel &vl = a.v[v];
-            vl.I0 = I0[v][l];
-            vl.I1 = I1[v][l];
-            vl.pitch0 = P0[v][l];
-            vl.pitch1 = P1[v][l];
-            vl.lo = l == 0 ? nullptr : (const uint16_t *)(base + L.lo[v][l]);
-            vl.C = base + L.C[v];
-            vl.S = (uint16_t *)(base + L.S[v]);
-            vl.d = (uint16_t *)(base + L.d[v][l]);
-            vl.S2 = nullptr;
-        }
+        LevelArgs a = level_args(p, pp, base, l, tune, gate);
         a.edge = (learned && l == top) ? edge : nullptr;
         if (learned && l == top) {
             // windows of the finest level from the network's prediction at the top level
@@ -374,20 +436,7 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
                                         a.D, a.Dw, (uint16_t *)(base + L.lo[v][l]), s);
         } else if (l > 0) {
             HookScope hs(hook, MPV_STAGE_SEED, 1, s);
-            SeedArgs sa{};
-            sa.W = g.W[l];
-            sa.H = g.H[l];
-            sa.Wp = g.W[l - 1];
-            sa.Hp = g.H[l - 1];
-            sa.block = g.block[l];
-            sa.Dw = g.Dw[l];
-            sa.D = g.D[l];
-            sa.nviews = nviews;
-            sa.gate = gate;
-            for (int v = 0; v < nviews; ++v) {
-                sa.dprev[v] = (const uint16_t *)(base + L.d[v][l - 1]);
-                sa.lo[v] = (uint16_t *)(base + L.lo[v][l]);
-            }
+            const SeedArgs sa = seed_args(pp, base, l, gate, tune.err);
             launch_seed(sa, s);
         }
         {

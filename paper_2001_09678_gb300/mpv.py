@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmpv.so")
+# MPV_LIBRARY selects another build of the library (the bounds-checked libmpv_debug.so)
+LIB_PATH = os.environ.get("MPV_LIBRARY") or os.path.join(HERE, "libmpv.so")
 
 MPV_OK = 0
 MPV_ERR_INVALID_ARG = 1
@@ -31,6 +32,9 @@ MPV_PROPOSAL_LEARNED = 1
 MPV_FALLBACK_NONE = 0
 MPV_FALLBACK_PYRAMID = 1
 MPV_FALLBACK_FULL = 2
+MPV_BATCH_AUTO = 0
+MPV_BATCH_PERSISTENT = 1
+MPV_BATCH_STREAMS = 2
 
 
 class MpvError(RuntimeError):
@@ -97,7 +101,7 @@ EXPORTS = [
     "mpv_cnn_conv3x3", "mpv_cnn_conv3x3_wgrad", "mpv_cnn_flip_transpose",
     "mpv_cnn_relu_backward", "mpv_cnn_huber", "mpv_cnn_adam", "mpv_cnn_to_bf16",
     "mpv_cnn_target", "mpv_proposal_features", "mpv_proposal_stats", "mpv_proposal_predict",
-    "mpv_proposal_fallbacks",
+    "mpv_proposal_fallbacks", "mpv_batch_info", "mpv_debug_batch_stall", "mpv_set_batch_mode",
 ]
 MPV_NOALLOC_SCRATCH_BYTES = 64 << 20
 MPV_STAGES = ("pyramid", "seed", "cost", "aggregate", "wta", "lr")
@@ -159,6 +163,9 @@ def load(path: str = LIB_PATH):
     L.mpv_proposal_features.argtypes = [ctx, vp, vp, i32, i32, i32, i32, vp, vp]
     L.mpv_proposal_stats.argtypes = [ctx, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     L.mpv_proposal_fallbacks.argtypes = [ctx, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+    L.mpv_batch_info.argtypes = [ctx] + [C.POINTER(i32)] * 4 + [C.POINTER(C.c_float)] * 2
+    L.mpv_debug_batch_stall.argtypes = [ctx, C.c_int64]
+    L.mpv_set_batch_mode.argtypes = [ctx, i32]
     L.mpv_destroy.argtypes = [ctx]
     L.mpv_destroy.restype = None
     L.mpv_server_destroy.restype = None
@@ -471,6 +478,22 @@ def mpv_proposal_stats(ctx):
     _check(load().mpv_proposal_stats(ctx, C.byref(a), C.byref(b)), "mpv_proposal_stats")
     return a.value, b.value
 
+
+
+def mpv_batch_info(ctx):
+    """(persistent, lanes, queues, cost_blocks, persistent_ms, streams_ms) of the
+    context's last batch."""
+    v = [C.c_int32() for _ in range(4)] + [C.c_float() for _ in range(2)]
+    _check(load().mpv_batch_info(ctx, *[C.byref(x) for x in v]), "mpv_batch_info")
+    return tuple(x.value for x in v)
+
+
+def mpv_set_batch_mode(ctx, mode: int) -> None:
+    _check(load().mpv_set_batch_mode(ctx, int(mode)), "mpv_set_batch_mode")
+
+
+def mpv_debug_batch_stall(ctx, wait_cycles: int) -> None:
+    _check(load().mpv_debug_batch_stall(ctx, int(wait_cycles)), "mpv_debug_batch_stall")
 
 
 def mpv_proposal_fallbacks(ctx):

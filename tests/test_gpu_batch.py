@@ -133,16 +133,76 @@ def test_mixed_batch_of_64(mpv):
         images = pool.map(_gen, specs)
         want = dict(zip(order, oracle_async.get()))
     pairs = [(L, R, spec[3]) for (L, R), spec in zip(images, specs)]
-    ctx = mpv.mpv_create(0)
-    try:
-        mpv.mpv_set_params(ctx, mpv.mpv_default_params(max_disparity=128, **BASE))
-        runs = _run_batch(mpv, ctx, pairs, repeats=2)
-    finally:
-        mpv.mpv_destroy(ctx)
+    runs = {}
+    for mode in ("PERSISTENT", "STREAMS"):          # both batch paths
+        ctx = mpv.mpv_create(0)
+        try:
+            mpv.mpv_set_params(ctx, mpv.mpv_default_params(max_disparity=128, **BASE))
+            mpv.mpv_set_batch_mode(ctx, getattr(mpv, "MPV_BATCH_" + mode))
+            runs[mode] = _run_batch(mpv, ctx, pairs, repeats=2)
+            assert mpv.mpv_batch_info(ctx)[0] == (mode == "PERSISTENT")
+        finally:
+            mpv.mpv_destroy(ctx)
     for i in range(64):
-        assert np.array_equal(runs[0][i], want[i]), f"pair {i} differs from the oracle"
+        for mode, r in runs.items():
+            assert np.array_equal(r[0][i], want[i]), f"pair {i} ({mode}) differs from the oracle"
+    runs = runs["PERSISTENT"]
     for i, (L, R, D) in enumerate(pairs):
         assert np.array_equal(runs[0][i], runs[1][i]), f"pair {i}: replay differs"
     for i in (1, 20, 50):
         L, R, D = pairs[i]
         assert np.array_equal(runs[0][i], _single(mpv, L, R, D)), f"pair {i}: batch != alone"
+
+
+def test_persistent_batch_and_its_bounded_wait(mpv):
+    # batches of supported pairs run through the persistent kernel; a stage that can
+    # never complete ends the launch by the bounded wait (about 1 ms here) with
+    # MPV_ERR_TIMEOUT from mpv_sync, and the context matches correctly afterwards
+    specs = [(160, 96, 32, 11), (200, 120, 48, 12), (96, 64, 16, 13), (256, 144, 64, 14)]
+    pairs = [(synth.slanted_pair(W, H, seed=s, d_max=D - 4)[:2]) + (D,) for W, H, D, s in specs]
+    want = [_oracle(L, R, D) for L, R, D in pairs]
+    ctx = mpv.mpv_create(0)
+    try:
+        mpv.mpv_set_params(ctx, mpv.mpv_default_params(max_disparity=128, **BASE))
+        mpv.mpv_set_batch_mode(ctx, mpv.MPV_BATCH_PERSISTENT)
+        # other content through the same workspace first: every launch must clear what it
+        # accumulates into, whatever the memory held before
+        _run_batch(mpv, ctx, [(R, L, D) for L, R, D in pairs], repeats=1)
+        runs = _run_batch(mpv, ctx, pairs, repeats=2)
+        persistent, lanes, queues, cb, pms, sms = mpv.mpv_batch_info(ctx)
+        assert persistent == 1 and lanes in (4, 8) and queues in (16, 32) and cb in (2, 8)
+        assert pms > 0 and sms > 0                     # the tuner timed both paths
+        for run in runs:
+            for got, w in zip(run, want):
+                assert np.array_equal(got, w)
+        mpv.mpv_debug_batch_stall(ctx, 2_000_000)
+        tens = [dict(left=torch.from_numpy(L).cuda(), right=torch.from_numpy(R).cuda(),
+                     disp=torch.full(L.shape, -2, dtype=torch.int16, device="cuda"),
+                     max_disparity=D) for L, R, D in pairs]
+        mpv.mpv_match_batch(ctx, tens)
+        with pytest.raises(mpv.MpvError) as e:
+            mpv.mpv_sync(ctx)
+        assert e.value.status == mpv.MPV_ERR_TIMEOUT
+        mpv.mpv_sync(ctx)                              # reported once
+        runs = _run_batch(mpv, ctx, pairs, repeats=1)  # still usable, still exact
+        for got, w in zip(runs[0], want):
+            assert np.array_equal(got, w)
+    finally:
+        mpv.mpv_destroy(ctx)
+
+
+def test_stream_path_when_persistent_does_not_apply(mpv):
+    # a gradient table is outside the persistent kernel: the batch runs as a graph of
+    # streams and still equals the oracle
+    pairs = [synth.slanted_pair(160, 96, seed=21 + i, d_max=28)[:2] + (32,) for i in range(3)]
+    lut = np.full(256, 10, np.int32)
+    ctx = mpv.mpv_create(0)
+    try:
+        mpv.mpv_set_params(ctx, mpv.mpv_default_params(max_disparity=32, **BASE))
+        mpv.mpv_set_gradient_penalty(ctx, lut)
+        runs = _run_batch(mpv, ctx, pairs, repeats=1)
+        assert mpv.mpv_batch_info(ctx)[0] == 0
+    finally:
+        mpv.mpv_destroy(ctx)
+    for (L, R, D), got in zip(pairs, runs[0]):
+        assert np.array_equal(got, _oracle(L, R, D))

@@ -135,3 +135,30 @@ def test_training_reduces_loss(m):
     t = torch.from_numpy((0.5 + 0.5 * xn[:, :1]).astype(np.float32)).cuda()
     losses = [net.train_step(x, t, 3e-3, 1.0 / 128).item() for _ in range(60)]
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_resumed_training_equals_uninterrupted(m, tmp_path):
+    # one 16x16 sample: the weight gradient is one block's sums (no atomic reordering), so
+    # training is bitwise reproducible and a resumed run must equal an uninterrupted one
+    from paper_2001_09678_gb300 import learn
+    rng = np.random.default_rng(9)
+    xn = rng.uniform(-0.5, 0.5, size=(1, 34, 16, 16)).astype(np.float32)
+    x = _bf(xn)
+    t = torch.from_numpy((0.5 + 0.5 * xn[:, :1]).astype(np.float32)).cuda()
+    a = learn.Net(learn.init_weights(34, seed=10))
+    for _ in range(5):
+        a.train_step(x, t, 2e-3, 1.0 / 128)
+    path = str(tmp_path / "mid.ckpt")
+    learn.save_checkpoint(path, dict(layers=a.numpy_layers(), adam=a.adam_state(), step=a.step,
+                                     pairs=0, samples=0, next_seed=0, rng=b"", D=128, factor=4))
+    for _ in range(5):
+        a.train_step(x, t, 2e-3, 1.0 / 128)
+    b = learn.Net.from_checkpoint(learn.load_checkpoint(path))
+    assert b.step == 5
+    for _ in range(5):
+        b.train_step(x, t, 2e-3, 1.0 / 128)
+    torch.cuda.synchronize()
+    assert a.step == b.step == 10
+    for La, Lb in zip(a.layers, b.layers):
+        for k in ("w", "b", "wb", "mw", "vw", "mb", "vb"):
+            assert torch.equal(La[k], Lb[k]), k
