@@ -229,16 +229,19 @@ def replica_throughput(units_per_step, steps, world, slowest_ms):
     return world * steps * units_per_step / (slowest_ms / 1e3) / 1e6
 
 
-def code_hash(path):
-    """sha256 prefix of a C/CUDA source with its comments, trailing blanks and empty lines
-    removed: edits to comments leave it unchanged, edits to code do not."""
+def code_hash(*paths):
+    """sha256 prefix of C/CUDA sources (in the given order) with their comments, trailing
+    blanks and empty lines removed: edits to comments leave it unchanged, edits to code do
+    not."""
     import hashlib
     import re
-    text = open(path, encoding="utf-8").read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
-    code = "\n".join(ln for ln in lines if ln)
-    return hashlib.sha256(code.encode("utf-8")).hexdigest()[:16]
+    parts = []
+    for path in paths:
+        text = open(path, encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+        parts.append("\n".join(ln for ln in lines if ln))
+    return hashlib.sha256("\n".join(parts).encode("utf-8")).hexdigest()[:16]
 
 
 def measured_counters(kernel):
@@ -254,8 +257,9 @@ def measured_counters(kernel):
             continue
         kv = dict(f.split("=", 1) for f in line.split())
         if "code_sha256_16" in kv:
-            src = os.path.join(ROOT, kv["source"])
-            src_ok = os.path.exists(src) and code_hash(src) == kv["code_sha256_16"]
+            srcs = [os.path.join(ROOT, f) for f in kv["source"].split(",")]
+            src_ok = (all(os.path.exists(f) for f in srcs) and
+                      code_hash(*srcs) == kv["code_sha256_16"])
             continue
         rows.append({k: float(v) for k, v in kv.items() if k != "level"})
     if not src_ok or not rows:
@@ -597,10 +601,16 @@ def measure_batch64(steps, warmup, serial=True):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
+    persistent, lanes, queues, cblocks, p_ms, s_ms = mpv.mpv_batch_info(ctx)
     mpv.mpv_destroy(ctx)
     out = {"value": round(units / ms / 1e3, 1), "unit": UNIT, "ms_per_batch": round(ms, 3),
            "pairs_per_s": round(64e3 / ms, 1), "steps": steps, "warmup": warmup,
-           "setup_s": round(setup_s, 2)}
+           "setup_s": round(setup_s, 2),
+           # the batch autotuner's measurements: the persistent kernel (best shapes) and the
+           # stream graph on this batch, and the path it kept
+           "path": "persistent kernel" if persistent else "stream graph",
+           "tuner_ms": {"persistent": round(p_ms, 3), "streams": round(s_ms, 3)},
+           "persistent_shapes": {"lanes": lanes, "queues": queues, "cost_blocks": cblocks}}
     if serial:
         seq_ms = _serial_ms(mpv, pairs, stream, max(1, steps // 4), warmup)
         out.update({"serial_ms_per_64_pairs": round(seq_ms, 3),
