@@ -229,7 +229,8 @@ mpv_status mpv_proposal_stats(const mpv_ctx *ctx, uint64_t *edge_hits, uint64_t 
 mpv_status mpv_proposal_fallbacks(const mpv_ctx *ctx, uint64_t *frames, uint64_t *fallbacks);
 
 /* Waits for the context's last submitted work and returns any latched device error,
- * MPV_ERR_TIMEOUT among them: the last persistent batch ended by its bounded wait.     */
+ * MPV_ERR_TIMEOUT among them: the last persistent batch ended by its bounded wait, or
+ * the learned proposal network's wait for its tensor-core products ran out.            */
 mpv_status mpv_sync(mpv_ctx *ctx);
 
 /* Batches (mpv_match_batch with n > 1) run either through one persistent kernel over a
@@ -346,7 +347,10 @@ void mpv_server_destroy(mpv_server *srv);
  * pointers, asynchronous on cuda_stream.  Invalid sizes return MPV_ERR_INVALID_ARG.   */
 
 /* out = conv3x3(in, weight[cout][cin][3][3]) + bias, optional ReLU; in is BF16, or FP32
- * when in_f32 = 1; cout is 32 or 1; out_bf16 and/or out_f32 receive the result.       */
+ * when in_f32 = 1; cout is 32 or 1; out_bf16 and/or out_f32 receive the result.
+ * BF16 input runs on the tensor cores (tcgen05, FP32 accumulation) while the operands
+ * fit in shared memory (cin up to 208); its one device wait is bounded, and outputs of
+ * tiles whose wait ran out are NaN.  Larger cin and FP32 input run on the CUDA cores.  */
 mpv_status mpv_cnn_conv3x3(const void *in, int32_t in_f32, int32_t n, int32_t cin, int32_t h,
                            int32_t w, const void *weight, const float *bias, int32_t cout,
                            int32_t relu, void *out_bf16, float *out_f32, void *cuda_stream);

@@ -252,200 +252,336 @@ __global__ void proposal_windows_kernel(const float *__restrict__ q, int Wq, int
 }
 
 
-// Tensor-core form of conv3x3_kernel<32, bf16> (inference and training forward): an
-// implicit GEMM  out[p][co] = sum_k A[p][k] B[k][co]  with p = pixel, k = (tap, ci).
-// The block stages the weights once as [co][tap][ci] and, for each of its row tiles, the
-// input tile channels-last in shared memory (channel stride CP, padded so that ldmatrix
-// rows fall in distinct banks); every warp multiplies 32 pixels x 32 channels with
-// mma.sync m16n8k16 (BF16 in, FP32 accumulate).  Row tile: 8 rows x 16 columns of
-// pixels, 4 warps of 2 rows each; kMmaRowTiles tiles per block share the staged weights.
-constexpr int kMmaRows = 8, kMmaCols = 16, kMmaRowTiles = 2;
+// Tensor-core form of conv3x3_kernel<32 or 1, bf16> (inference and training forward) on
+// the fifth-generation tensor cores: an implicit GEMM
+//     D[m][co] = sum_{tap, ci} A[m][(tap, ci)] B[co][(tap, ci)]
+// with m one of the 128 pixels of an output tile of 16 rows x 8 columns (M = 128), N = 32
+// output channels (16 for the one-channel output layer, its other rows zero weights) and
+// K = 9 taps x the input channels rounded up to 16, in k-steps of 16 (kind::f16, BF16
+// operands, FP32 accumulation in tensor memory).
+//
+// Shared memory holds both operands K-major without swizzling, as 8-row x 16-byte core
+// matrices.  The input tile with its one-pixel halo (18 x 10 pixels) is stored as planes of
+// 8 channels: plane c8 holds channels 8 c8 .. 8 c8 + 7 of every staged pixel, 16 bytes per
+// pixel, pixels row-major.  Eight consecutive output pixels of one row then form a core
+// matrix for every tap: the A operand of tap (ky, kx) starts at staged pixel ky * 10 + kx,
+// its core matrices follow each other along M at one staged row (160 bytes) and along K at
+// one plane.  The weights are stored [tap][c8][co][8], so that B's core matrices follow
+// each other along N at 8 channels (128 bytes) and along K at one plane of NC x 16 bytes.
+// One thread issues the 9 x (K/16) MMAs of a tile and commits them to an mbarrier; the
+// four warps read their 32 rows of the accumulator back (tcgen05.ld) for the epilogue.
+constexpr int kTcRows = 16, kTcCols = 8;                 // output tile (M = 128 pixels)
+constexpr int kTcTR = kTcRows + 2, kTcTC = kTcCols + 2;  // staged input tile, 18 x 10
+constexpr int kTcPix = kTcTR * kTcTC;
+// bytes of one plane of 8 channels; the extra 16 bytes spread one pixel's planes over banks
+constexpr int kTcPlane = kTcPix * 16 + 16;
+constexpr int kTcBlocksPerSm = 4;                        // resident blocks the grid aims for
+constexpr long long kTcWaitCycles = 2000000000LL;        // about a second
 
-__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
-                                        const void *p)
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x2(unsigned &r0, unsigned &r1, const void *p)
-{
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
-                 : "=r"(r0), "=r"(r1) : "r"(a));
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2,
-                                         unsigned a3, unsigned b0, unsigned b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// NT: n-tiles of 8 output channels (4: the 32-channel layers; 1: the output layer, its
-// one channel padded to 8 with zero weights)
-// NHWC: activations channels-last, [n][y][x][cstr] with the first Cin channels valid and
-// cstr a multiple of 8 (the pipeline's own buffers: 16-byte copies of whole pixels);
-// otherwise [n][c][y][x] (the public entry points).
-template <int NT, bool NHWC>
-__global__ void __launch_bounds__(128) conv3x3_mma_kernel(
-    const __nv_bfloat16 *__restrict__ in, int Cin, int cstr, int CP, int H, int W,
+// Shared-memory matrix descriptor of a K-major operand without swizzling: start address,
+// byte distance between core matrices adjacent along K (lbo) and along M or N (sbo), each
+// in 16-byte units, and the descriptor version of this architecture (bit 46).
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5), BF16 A and B (bits
+// 7-9, 10-12), both K-major (bits 15, 16 clear), N / 8 (bits 17-22), M / 16 (bits 24-28).
+template <int M, int N>
+__host__ __device__ constexpr uint32_t umma_instr_desc()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_phase_done(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 32 lanes x X columns of 32 bits from tensor memory: thread t of the warp gets lane
+// (warp's first lane + t), columns col .. col + X - 1
+template <int X>
+struct TmemRow;
+template <>
+struct TmemRow<32> {
+    __device__ __forceinline__ static void ld(uint32_t taddr, uint32_t (&r)[32])
+    {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+            "%26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+              "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    }
+};
+template <>
+struct TmemRow<16> {
+    __device__ __forceinline__ static void ld(uint32_t taddr, uint32_t (&r)[16])
+    {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
+};
+
+size_t tc_smem_bytes(int Cin, int Cout)
+{
+    const int ncg = tc_planes(Cin), nc = tc_width(Cout);
+    return (size_t)ncg * kTcPlane + (size_t)9 * ncg * nc * 16 + 16;
+}
+
+// NC: the MMA width N (32, or 16 for the one-channel output layer).
+// NHWC: activations [n][y][x][cstr] (cstr a multiple of 8, channels Cin .. cstr - 1 zero)
+// and weights pre-arranged [9][tc_planes(Cin)][NC][8] with zero padding (the matcher's own
+// buffers); otherwise activations [n][c][y][x] and weights [Cout][Cin][3][3] (the public
+// entry points).  err (optional): set to 1 when the wait for the tensor cores ran out; the
+// outputs of the block's unfinished tiles are then NaN.
+template <int NC, bool NHWC>
+__global__ void __launch_bounds__(128) conv3x3_tc_kernel(
+    const __nv_bfloat16 *__restrict__ in, int Cin, int cstr, int H, int W, int nimg,
     const __nv_bfloat16 *__restrict__ w, const float *__restrict__ b, int Cout, int relu,
-    __nv_bfloat16 *__restrict__ out_bf, float *__restrict__ out_f)
+    __nv_bfloat16 *__restrict__ out_bf, float *__restrict__ out_f, int *err)
 {
-    constexpr int NC = 8 * NT;                           // output channels of the tile
-    extern __shared__ __align__(16) __nv_bfloat16 sm[];
-    constexpr int TR = kMmaRows + 2, TC = kMmaCols + 2;
-    __nv_bfloat16 *xs = sm;                              // [TR][TC][CP]
-    __nv_bfloat16 *ws = sm + TR * TC * CP;               // [NC][9][CP]
-    const int n = blockIdx.z;
-    const int x0 = blockIdx.x * kMmaCols;
-    const int64_t plane = (int64_t)H * W;
-    const __nv_bfloat16 *src = in + (int64_t)n * (NHWC ? cstr : Cin) * plane;
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    const int K16 = (Cin + 15) / 16 * 16;                // channels the k-steps cover
+    extern __shared__ __align__(128) unsigned char tsm[];
+    const int ncg = tc_planes(Cin), ks = ncg / 2;
+    unsigned char *As = tsm;                                   // ncg planes
+    unsigned char *Bs = tsm + (size_t)ncg * kTcPlane;          // [9][ncg][NC][8]
+    uint64_t *mbar = (uint64_t *)(Bs + (size_t)9 * ncg * NC * 16);
+    uint32_t *tslot = (uint32_t *)(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // the planes start zero: channels the staging never writes (Cin or cstr up to the
+    // k-steps' multiple of 16) stay zero in every tile
+    for (int i = tid; i < ncg * kTcPlane / 16; i += 128)
+        ((uint4 *)As)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (NHWC) {
-        // weights already in this layout (zero padding included): 16-byte copies
-        const uint4 *wsrc = (const uint4 *)w;
-        uint4 *wdst = (uint4 *)ws;
-        const int nvec = NC * 9 * CP / 8;
-        for (int i = threadIdx.x; i < nvec; i += 128) wdst[i] = wsrc[i];
-    } else
-    // weights: one (co, ci) pair per step, its 9 taps contiguous in global memory;
-    // output channels Cout .. NC-1 have zero weights
-    for (int i0 = threadIdx.x; i0 < NC * Cin; i0 += 256) {   // two pairs per round
-        __nv_bfloat16 v[2][9];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int i = i0 + h * 128;
-            const int co = i / Cin;
-            const __nv_bfloat16 *wr = w + (int64_t)i * 9;
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap)
-                v[h][tap] = (i < NC * Cin && co < Cout) ? wr[tap] : zero;
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int i = i0 + h * 128;
-            if (i >= NC * Cin) break;
-            const int co = i / Cin, c = i - co * Cin;
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) ws[(co * 9 + tap) * CP + c] = v[h][tap];
+        const int nvec = 9 * ncg * NC;
+        for (int i = tid; i < nvec; i += 128) ((uint4 *)Bs)[i] = ((const uint4 *)w)[i];
+    } else {
+        // element (tap, ci, co) at ((tap * ncg + ci / 8) * NC + co) * 8 + ci % 8, zero for
+        // absent channels
+        __nv_bfloat16 *bw = (__nv_bfloat16 *)Bs;
+        const __nv_bfloat16 zero = __float2bfloat16(0.f);
+        const int ntot = 9 * ncg * 8 * NC;
+        for (int i = tid; i < ntot; i += 128) {
+            const int co = i % NC, r = i / NC, ci = r % (ncg * 8), tap = r / (ncg * 8);
+            bw[((tap * ncg + ci / 8) * NC + co) * 8 + ci % 8] =
+                (co < Cout && ci < Cin) ? w[((int64_t)co * Cin + ci) * 9 + tap] : zero;
         }
     }
-    // channels Cin .. K16-1 are zero in both operands (never rewritten below)
-    const int npad = K16 - Cin;
-    if (!NHWC)
-        for (int i = threadIdx.x; i < NC * 9 * npad; i += 128)
-            ws[(i / npad) * CP + Cin + i % npad] = zero;
-    for (int i = threadIdx.x; i < TR * TC * npad; i += 128)
-        xs[(i / npad) * CP + Cin + i % npad] = zero;
+    if (warp == 0) {   // 32 columns of tensor memory: the 128 x NC FP32 accumulator
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+                         smem_addr(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // ldmatrix row addresses: A rows = pixels of row (2*warp + mt), B rows = channels
-    const int arow = lane & 15, acol = (lane >> 4) * 8;
-    const int brow = lane & 7, bcol = ((lane >> 3) & 1) * 8;
-    const int g = lane >> 2, t = lane & 3;
-    for (int rt = 0; rt < kMmaRowTiles; ++rt) {
-        const int y0 = (blockIdx.y * kMmaRowTiles + rt) * kMmaRows;
-        if (y0 >= H) break;                              // uniform over the block
-        __syncthreads();                                 // the previous tile is consumed
+    const int tx = (W + kTcCols - 1) / kTcCols, ty = (H + kTcRows - 1) / kTcRows;
+    const int ntiles = tx * ty * nimg;
+    const int64_t plane = (int64_t)H * W;
+    constexpr uint32_t idesc = umma_instr_desc<128, NC>();
+    const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs), mb = smem_addr(mbar);
+    uint32_t phase = 0;
+    int tile = blockIdx.x;
+    bool failed = false;
+
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int n = tile / (tx * ty), r = tile - n * (tx * ty);
+        const int y0 = (r / tx) * kTcRows, x0 = (r % tx) * kTcCols;
+        // the input tile with its one-pixel halo, zero outside the image, in 16-byte pieces
+        // (8 channels of one pixel); consecutive threads on consecutive pieces, a batch of
+        // loads before the stores
+        constexpr int kBatch = 8;
         if (NHWC) {
-            // whole pixels in 16-byte pieces (cstr / 8 per pixel), consecutive threads on
-            // consecutive pieces, a batch of loads before the stores
-            constexpr int kBatch = 8;
-            const int per = cstr / 8, npieces = TR * TC * per;
-            for (int i0 = threadIdx.x; i0 < npieces; i0 += 128 * kBatch) {
+            const __nv_bfloat16 *src = in + (int64_t)n * cstr * plane;
+            const int per = cstr / 8, npieces = kTcPix * per;
+            for (int i0 = tid; i0 < npieces; i0 += 128 * kBatch) {
                 uint4 v[kBatch];
 #pragma unroll
-                for (int b2 = 0; b2 < kBatch; ++b2) {
-                    const int i = i0 + b2 * 128;
-                    const int pp = i / per, q = i - pp * per;
-                    const int py = pp / TC, px = pp - py * TC;
+                for (int q = 0; q < kBatch; ++q) {
+                    const int i = i0 + q * 128;
+                    const int pp = i / per, c8 = i - pp * per;
+                    const int py = pp / kTcTC, px = pp - py * kTcTC;
                     const int yy = y0 - 1 + py, xx = x0 - 1 + px;
-                    v[b2] = make_uint4(0u, 0u, 0u, 0u);
+                    v[q] = make_uint4(0u, 0u, 0u, 0u);
                     if (i < npieces && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                        v[b2] = *(const uint4 *)(src + ((int64_t)yy * W + xx) * cstr + 8 * q);
+                        v[q] = *(const uint4 *)(src + ((int64_t)yy * W + xx) * cstr + 8 * c8);
                 }
 #pragma unroll
-                for (int b2 = 0; b2 < kBatch; ++b2) {
-                    const int i = i0 + b2 * 128;
+                for (int q = 0; q < kBatch; ++q) {
+                    const int i = i0 + q * 128;
                     if (i >= npieces) break;
-                    const int pp = i / per, q = i - pp * per;
-                    *(uint4 *)(xs + pp * CP + 8 * q) = v[b2];
+                    const int pp = i / per, c8 = i - pp * per;
+                    *(uint4 *)(As + c8 * kTcPlane + pp * 16) = v[q];
                 }
             }
         } else {
-        // input tile, consecutive threads on consecutive pixels of a row; each thread
-        // issues kStageBatch loads before its stores, so that their latencies overlap
-        constexpr int kStageBatch = 8;
-        const int ntile = TR * TC * Cin;
-        for (int i0 = threadIdx.x; i0 < ntile; i0 += 128 * kStageBatch) {
-            __nv_bfloat16 v[kStageBatch];
-            int dst[kStageBatch];
-#pragma unroll
-            for (int b = 0; b < kStageBatch; ++b) {
-                const int i = i0 + b * 128;
-                const int px = i % TC, q = i / TC, py = q % TR, c = q / TR;
+            // piece (plane c8, pixel pp): consecutive threads on consecutive pixels, each
+            // gathering its 8 channels from 8 channel planes of the image
+            const __nv_bfloat16 *src = in + (int64_t)n * Cin * plane;
+            const int cgi = (Cin + 7) / 8, npieces = kTcPix * cgi;
+            for (int i = tid; i < npieces; i += 128) {
+                const int c8 = i / kTcPix, pp = i - c8 * kTcPix;
+                const int py = pp / kTcTC, px = pp - py * kTcTC;
                 const int yy = y0 - 1 + py, xx = x0 - 1 + px;
-                const bool in_img = i < ntile && yy >= 0 && yy < H && xx >= 0 && xx < W;
-                v[b] = in_img ? src[c * plane + (int64_t)yy * W + xx] : zero;
-                dst[b] = i < ntile ? (py * TC + px) * CP + c : -1;
-            }
+                uint32_t pk[4] = {0u, 0u, 0u, 0u};
+                if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                    const __nv_bfloat16 *s0 = src + (int64_t)(8 * c8) * plane + (int64_t)yy * W + xx;
+                    unsigned short h[8];
 #pragma unroll
-            for (int b = 0; b < kStageBatch; ++b)
-                if (dst[b] >= 0) xs[dst[b]] = v[b];
+                    for (int e = 0; e < 8; ++e)
+                        h[e] = 8 * c8 + e < Cin ? __bfloat16_as_ushort(s0[(int64_t)e * plane]) : 0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) pk[e] = (uint32_t)h[2 * e] | ((uint32_t)h[2 * e + 1] << 16);
+                }
+                *(uint4 *)(As + c8 * kTcPlane + pp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
         }
-        }
+        // the staged tile, written through the generic proxy, before the tensor cores read it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        float acc[2][NT][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
-        for (int tap = 0; tap < 9; ++tap) {
-            const int ky = tap / 3, kx = tap % 3;
-            for (int c0 = 0; c0 < K16; c0 += 16) {
-                unsigned a[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int py = 2 * warp + mt + ky, px = arow + kx;
-                    ldsm_x4(a[mt][0], a[mt][1], a[mt][2], a[mt][3],
-                            xs + (py * TC + px) * CP + c0 + acol);
-                }
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    unsigned b0, b1;
-                    ldsm_x2(b0, b1, ws + ((nt * 8 + brow) * 9 + tap) * CP + c0 + bcol);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt)
-                        mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int tap = 0; tap < 9; ++tap) {
+                const uint32_t aoff = (uint32_t)(((tap / 3) * kTcTC + tap % 3) * 16);
+                for (int s = 0; s < ks; ++s) {
+                    const uint64_t ad =
+                        umma_smem_desc(a0 + 2 * s * kTcPlane + aoff, kTcPlane, kTcTC * 16);
+                    const uint64_t bd = umma_smem_desc(
+                        b0 + (uint32_t)((tap * ncg + 2 * s) * NC * 16), NC * 16, 128);
+                    umma_bf16(tmem, ad, bd, idesc, (tap | s) != 0);
                 }
             }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    mb)
+                : "memory");
         }
-        // accumulator layout: d0,d1 at (row g, cols 2t, 2t+1), d2,d3 at (row g+8, same cols)
+        // the products (bounded wait; the block agrees on the outcome)
+        bool ok = mbar_phase_done(mb, phase);
+        if (!ok) {
+            const long long t0 = clock64();
+            while (!(ok = mbar_phase_done(mb, phase)) && clock64() - t0 < kTcWaitCycles) {
+            }
+        }
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t acc[NC];
+        TmemRow<NC>::ld(tmem + ((uint32_t)(warp * 32) << 16), acc);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // accumulator row m = 32 warp + lane: output pixel (y0 + m / 8, x0 + m % 8)
+        const int m = warp * 32 + lane;
+        const int oy = y0 + m / kTcCols, ox = x0 + m % kTcCols;
+        if (oy < H && ox < W) {
+            const int64_t pix = (int64_t)oy * W + ox;
+            bool done = false;
+            if constexpr (NC == 32 && NHWC) {
+                if (Cout == 32 && out_bf && !out_f) {   // the matcher's hidden layers
+                    uint4 *dst = (uint4 *)(out_bf + ((int64_t)n * plane + pix) * 32);
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int y = y0 + 2 * warp + mt;
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t pk[4];
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
+                        for (int e = 0; e < 4; ++e) {
+                            const int co = 8 * q + 2 * e;
+                            float v0 = __uint_as_float(acc[co]) + (b ? b[co] : 0.f);
+                            float v1 = __uint_as_float(acc[co + 1]) + (b ? b[co + 1] : 0.f);
+                            if (relu) {
+                                v0 = fmaxf(v0, 0.f);
+                                v1 = fmaxf(v1, 0.f);
+                            }
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                            pk[e] = *(const uint32_t *)&h2;
+                        }
+                        dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                    done = true;
+                }
+            }
+            if (!done) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int x = x0 + g + (e >= 2 ? 8 : 0);
-                    const int co = nt * 8 + 2 * t + (e & 1);
-                    if (x >= W || y >= H || co >= Cout) continue;
-                    float v = acc[mt][nt][e] + (b ? b[co] : 0.f);
+                for (int co = 0; co < NC; ++co) {
+                    if (co >= Cout) break;
+                    float v = __uint_as_float(acc[co]) + (b ? b[co] : 0.f);
                     if (relu) v = fmaxf(v, 0.f);
-                    const int64_t o = NHWC ? ((int64_t)n * plane + (int64_t)y * W + x) * Cout + co
-                                           : ((int64_t)n * Cout + co) * plane + (int64_t)y * W + x;
+                    const int64_t o = NHWC ? ((int64_t)n * plane + pix) * Cout + co
+                                           : ((int64_t)n * Cout + co) * plane + pix;
                     if (out_f) out_f[o] = v;
                     if (out_bf) out_bf[o] = __float2bfloat16(v);
                 }
+            }
+        }
+        // every warp's reads of the accumulator and of the staged tile are complete before
+        // the next tile overwrites them
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (failed) {
+        // the wait ran out: record it, and mark the block's unfinished tiles as NaN
+        if (tid == 0 && err) atomicCAS(err, 0, 1);
+        for (; tile < ntiles; tile += gridDim.x) {
+            const int n = tile / (tx * ty), r = tile - n * (tx * ty);
+            const int oy = (r / tx) * kTcRows + tid / kTcCols, ox = (r % tx) * kTcCols + tid % kTcCols;
+            if (oy >= H || ox >= W) continue;
+            const int64_t pix = (int64_t)oy * W + ox;
+            for (int co = 0; co < Cout && co < NC; ++co) {
+                const int64_t o = NHWC ? ((int64_t)n * plane + pix) * Cout + co
+                                       : ((int64_t)n * Cout + co) * plane + pix;
+                if (out_f) out_f[o] = __int_as_float(0x7FC00000);
+                if (out_bf) out_bf[o] = __ushort_as_bfloat16((unsigned short)0x7FC0);
+            }
         }
     }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -470,47 +606,63 @@ void launch_conv3x3_t(const TIn *in, int N, int Cin, int H, int W, const __nv_bf
     }
 }
 
-template <bool NHWC>
-void launch_mma(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
-                const __nv_bfloat16 *w, const float *b, int Cout, int relu, __nv_bfloat16 *out_bf,
-                float *out_f, cudaStream_t s)
+int sm_count()
 {
-    // channel stride: Cin rounded up to 16 (whole k-steps) plus 8 (bank spread)
-    const int CP = mma_channel_stride(Cin);
-    const int NC = Cout == 32 ? 32 : 8;
-    const size_t smem =
-        sizeof(__nv_bfloat16) * (size_t)CP * ((kMmaRows + 2) * (kMmaCols + 2) + NC * 9);
-    const int rows = kMmaRows * kMmaRowTiles;
-    dim3 grid((W + kMmaCols - 1) / kMmaCols, (H + rows - 1) / rows, N);
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n < 1) n = 1;
+    }
+    return n;
+}
+
+template <bool NHWC>
+void launch_tc(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
+               const __nv_bfloat16 *w, const float *b, int Cout, int relu, __nv_bfloat16 *out_bf,
+               float *out_f, int *err, cudaStream_t s)
+{
+    const int64_t tiles = (int64_t)((W + kTcCols - 1) / kTcCols) * ((H + kTcRows - 1) / kTcRows) * N;
+    const int64_t cap = (int64_t)kTcBlocksPerSm * sm_count();
+    const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+    const size_t smem = tc_smem_bytes(Cin, Cout);
     if (Cout == 32) {
-        cudaFuncSetAttribute(conv3x3_mma_kernel<4, NHWC>,
+        cudaFuncSetAttribute(conv3x3_tc_kernel<32, NHWC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        conv3x3_mma_kernel<4, NHWC><<<grid, 128, smem, s>>>(in, Cin, cstr, CP, H, W, w, b, Cout,
-                                                            relu, out_bf, out_f);
+        conv3x3_tc_kernel<32, NHWC><<<grid, 128, smem, s>>>(in, Cin, cstr, H, W, N, w, b, Cout,
+                                                            relu, out_bf, out_f, err);
     } else {
-        cudaFuncSetAttribute(conv3x3_mma_kernel<1, NHWC>,
+        cudaFuncSetAttribute(conv3x3_tc_kernel<16, NHWC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        conv3x3_mma_kernel<1, NHWC><<<grid, 128, smem, s>>>(in, Cin, cstr, CP, H, W, w, b, Cout,
-                                                            relu, out_bf, out_f);
+        conv3x3_tc_kernel<16, NHWC><<<grid, 128, smem, s>>>(in, Cin, cstr, H, W, N, w, b, Cout,
+                                                            relu, out_bf, out_f, err);
     }
 }
 
 void launch_conv3x3_nhwc(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
                          const __nv_bfloat16 *w, const float *b, int Cout, int relu,
-                         __nv_bfloat16 *out_bf, float *out_f, cudaStream_t s)
+                         __nv_bfloat16 *out_bf, float *out_f, int *err, cudaStream_t s)
 {
-    launch_mma<true>(in, N, Cin, cstr, H, W, w, b, Cout, relu, out_bf, out_f, s);
+    launch_tc<true>(in, N, Cin, cstr, H, W, w, b, Cout, relu, out_bf, out_f, err, s);
+}
+
+bool conv3x3_tc_ok(int Cin, int Cout)
+{
+    return (Cout == 32 || Cout == 1) && tc_smem_bytes(Cin, Cout) <= kTcMaxSmem;
 }
 
 void launch_conv3x3(const __nv_bfloat16 *in, int N, int Cin, int H, int W, const __nv_bfloat16 *w,
                     const float *b, int Cout, int relu, __nv_bfloat16 *out_bf, float *out_f,
                     cudaStream_t s)
 {
-    if (Cout != 32 && Cout != 1) {
+    // widths the tensor-core tile covers (the network's 32 and 1 channels) with operands
+    // that fit in shared memory; any other shape on the CUDA cores
+    if (!conv3x3_tc_ok(Cin, Cout)) {
         launch_conv3x3_t(in, N, Cin, H, W, w, b, Cout, relu, out_bf, out_f, s);
         return;
     }
-    launch_mma<false>(in, N, Cin, Cin, H, W, w, b, Cout, relu, out_bf, out_f, s);
+    launch_tc<false>(in, N, Cin, Cin, H, W, w, b, Cout, relu, out_bf, out_f, nullptr, s);
 }
 
 void launch_conv3x3_wgrad(const __nv_bfloat16 *in, int N, int Cin, const float *g, int Cout, int H,
@@ -553,7 +705,8 @@ mpv_status mpv_cnn_conv3x3(const void *in, int32_t in_f32, int32_t n, int32_t ci
                            int32_t relu, void *out_bf16, float *out_f32, void *cuda_stream)
 {
     if (!in || !weight || n < 1 || cin < 1 || h < 1 || w < 1 || (cout != 32 && cout != 1) ||
-        (!out_bf16 && !out_f32) || conv_smem_bytes(cin, cout) > 200 * 1024)
+        (!out_bf16 && !out_f32) ||
+        ((in_f32 || !conv3x3_tc_ok(cin, cout)) && conv_smem_bytes(cin, cout) > 200 * 1024))
         return MPV_ERR_INVALID_ARG;
     if (in_f32)
         launch_conv3x3_t((const float *)in, n, cin, h, w, (const __nv_bfloat16 *)weight, bias,

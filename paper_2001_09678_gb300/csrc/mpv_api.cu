@@ -52,9 +52,12 @@ struct mpv_ctx {
     ProposalNet net;
     void *net_mem = nullptr;
     // pinned: window-edge hits and pixels of the last learned frame, learned frames and
-    // fallbacks since creation (copied from counters_dev after every learned frame)
+    // fallbacks since creation, and the network's wait status (copied from counters_dev
+    // after every learned frame)
     unsigned long long *edge_host = nullptr;
-    unsigned long long *counters_dev = nullptr;   // device: learned frames, fallbacks
+    // device: learned frames, fallbacks, the network's wait status (non-zero: the wait for
+    // the tensor cores ran out)
+    unsigned long long *counters_dev = nullptr;
     // gradient-weighted penalty: host copy and device copy of the 256 slopes
     bool grad_on = false;
     int32_t grad_host[256] = {};
@@ -598,7 +601,7 @@ mpv_status enqueue_direct(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, cons
             src = (const uint8_t *)ctx->ws + L.gate + offsetof(FallbackGate, hits);
         cudaMemcpyAsync(ctx->edge_host, src, 2 * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(ctx->edge_host + 2, ctx->counters_dev, 2 * sizeof(unsigned long long),
+        cudaMemcpyAsync(ctx->edge_host + 2, ctx->counters_dev, 3 * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost, s);
         r = cuda_status(cudaGetLastError());
     }
@@ -623,13 +626,13 @@ mpv_status enqueue(mpv_ctx *ctx, const PairJob &job, cudaStream_t s, const Stage
     const bool learned = ctx->p.proposal == MPV_PROPOSAL_LEARNED;
     if (learned && !ctx->net.layers) return MPV_ERR_INVALID_ARG;    // no weights loaded
     if (learned && !dbg && !ctx->edge_host) {
-        if (cudaMallocHost(&ctx->edge_host, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        if (cudaMallocHost(&ctx->edge_host, 5 * sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
             return MPV_ERR_OOM;
         }
-        for (int i = 0; i < 4; ++i) ctx->edge_host[i] = 0;
-        if (cudaMalloc(&ctx->counters_dev, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-            cudaMemset(ctx->counters_dev, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        for (int i = 0; i < 5; ++i) ctx->edge_host[i] = 0;
+        if (cudaMalloc(&ctx->counters_dev, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMemset(ctx->counters_dev, 0, 3 * sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
             cudaFreeHost(ctx->edge_host);
             ctx->edge_host = nullptr;
@@ -920,6 +923,7 @@ mpv_status mpv_load_proposal_weights(mpv_ctx *ctx, const char *path)
         net.relu[k] = rd(off + 8);
         const bool lastk = k == kProposalLayers - 1;
         if (net.cin[k] < 1 || net.cin[k] > 1024 || net.cout[k] != (lastk ? 1 : 32) ||
+            !conv3x3_tc_ok(net.cin[k], net.cout[k]) ||
             net.relu[k] != (lastk ? 0 : 1) || (k > 0 && net.cin[k] != net.cout[k - 1]))
             return MPV_ERR_INVALID_ARG;
         nw += (size_t)net.cout[k] * net.cin[k] * 9;
@@ -943,8 +947,8 @@ mpv_status mpv_load_proposal_weights(mpv_ctx *ctx, const char *path)
         iw += n;
         ib += net.cout[k];
     }
-    // the same weights in the tensor-core kernel's shared-memory layout, [NC][9][CP]
-    // (zero-padded output and input channels), copied whole by the matcher's network
+    // the same weights in the tensor-core kernel's layout [9][planes][width][8] (zero
+    // padded input and output channels), copied whole by the matcher's network
     std::vector<__nv_bfloat16> ht;
     size_t toff[kProposalLayers];
     {
@@ -952,13 +956,13 @@ mpv_status mpv_load_proposal_weights(mpv_ctx *ctx, const char *path)
         const __nv_bfloat16 zero = __float2bfloat16(0.f);
         for (int k = 0; k < kProposalLayers; ++k) {
             const int Cin = net.cin[k], Cout = net.cout[k];
-            const int NC = Cout == 32 ? 32 : 8, CP = mma_channel_stride(Cin);
+            const int planes = tc_planes(Cin), width = tc_width(Cout);
             toff[k] = ht.size();
-            ht.resize(ht.size() + (size_t)NC * 9 * CP, zero);
+            ht.resize(ht.size() + tc_weight_elems(Cin, Cout), zero);
             for (int co = 0; co < Cout; ++co)
                 for (int c = 0; c < Cin; ++c)
                     for (int tap = 0; tap < 9; ++tap)
-                        ht[toff[k] + ((size_t)co * 9 + tap) * CP + c] =
+                        ht[toff[k] + ((size_t)(tap * planes + c / 8) * width + co) * 8 + c % 8] =
                             hw[iw2 + ((size_t)co * Cin + c) * 9 + tap];
             iw2 += (size_t)Cout * Cin * 9;
         }
@@ -1110,6 +1114,11 @@ mpv_status mpv_sync(mpv_ctx *ctx)
     if (ctx->bstatus_host && *ctx->bstatus_host != MPV_OK) {   // a persistent batch's wait ran out
         ctx->latched = *ctx->bstatus_host;
         *ctx->bstatus_host = MPV_OK;
+    }
+    if (ctx->edge_host && ctx->edge_host[4] != 0) {   // the proposal network's wait ran out
+        ctx->latched = MPV_ERR_TIMEOUT;
+        ctx->edge_host[4] = 0;
+        cudaMemset(ctx->counters_dev + 2, 0, sizeof(unsigned long long));
     }
     const mpv_status st = (mpv_status)ctx->latched;
     ctx->latched = MPV_OK;

@@ -178,12 +178,24 @@ void launch_features(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const
 void launch_features_nhwc(const uint8_t *I0, int p0, const uint8_t *I1, int p1, const uint8_t *C,
                           int Dws, int Dw, int W, int H, int cstr, __nv_bfloat16 *out,
                           cudaStream_t s);
-// wt: the weights laid out [NC][9][mma_channel_stride(Cin)] (NC = 32, or 8 for Cout = 1)
+// Tensor-core convolution (tcgen05): 8-channel planes of the input channels rounded up to
+// whole k-steps of 16, and the MMA width for Cout output channels (32, or 16 for Cout = 1).
+__host__ __device__ inline int tc_planes(int Cin) { return (Cin + 15) / 16 * 2; }
+__host__ __device__ inline int tc_width(int Cout) { return Cout == 32 ? 32 : 16; }
+// elements of the weights in the kernel's layout [9][tc_planes(Cin)][tc_width(Cout)][8]
+// (element (tap, ci, co) at ((tap * planes + ci / 8) * width + co) * 8 + ci % 8, zero for
+// absent input or output channels)
+inline size_t tc_weight_elems(int Cin, int Cout)
+{
+    return (size_t)9 * tc_planes(Cin) * tc_width(Cout) * 8;
+}
+constexpr size_t kTcMaxSmem = 200 * 1024;   // shared memory the convolution may request
+bool conv3x3_tc_ok(int Cin, int Cout);
+// wt: the weights in the tensor-core layout above; err (optional): set to 1 when the wait
+// for the tensor cores ran out
 void launch_conv3x3_nhwc(const __nv_bfloat16 *in, int N, int Cin, int cstr, int H, int W,
                          const __nv_bfloat16 *wt, const float *b, int Cout, int relu,
-                         __nv_bfloat16 *out_bf, float *out_f, cudaStream_t s);
-// channel stride of the tensor-core convolution's shared tiles: whole k-steps plus 8
-inline int mma_channel_stride(int Cin) { return (Cin + 15) / 16 * 16 + 8; }
+                         __nv_bfloat16 *out_bf, float *out_f, int *err, cudaStream_t s);
 // channels per pixel of the network input in the matcher's buffers
 inline int feature_stride(int Dw_top) { return (2 + Dw_top + 7) / 8 * 8; }
 void launch_proposal_windows(const float *q, int Wq, int Hq, int f, int W, int H, int D, int Dw,

@@ -464,7 +464,8 @@ mpv_status enqueue_pair(const mpv_params &p, const PairJob &job, uint8_t *base, 
                 launch_conv3x3_nhwc(in, nviews, net->cin[k], cstr, a.H, a.W,
                                     (const __nv_bfloat16 *)net->wt[k], net->b[k], net->cout[k],
                                     net->relu[k], lastk ? nullptr : bufs[k & 1],
-                                    lastk ? (float *)(base + L.q) : nullptr, s);
+                                    lastk ? (float *)(base + L.q) : nullptr,
+                                    counters ? (int *)(counters + 2) : nullptr, s);
                 in = bufs[k & 1];
                 cstr = net->cout[k];
             }

@@ -39,6 +39,34 @@ def test_conv_forward_matches_oracle(m):
     assert np.all(np.abs(out.cpu().numpy() - want) <= 1e-5 * scale + 1e-6)
 
 
+@pytest.mark.parametrize("n,cin,cout,h,w,relu", [
+    (1, 5, 32, 17, 9, True),       # one k-step, most channels padding
+    (3, 32, 1, 45, 61, False),     # the output layer's width (one channel of 16)
+    (2, 33, 32, 30, 70, True),     # a ragged last k-step, ragged tiles in x and y
+    (1, 208, 32, 19, 21, True),    # the widest input the shared-memory operands hold
+    (2, 34, 32, 180, 320, True),   # the network's first layer at its size: more tiles
+])                                 # than blocks, so blocks loop over tiles
+def test_conv_tensor_core_shapes(m, n, cin, cout, h, w, relu):
+    # BF16 input with 32 or 1 output channels runs on the tcgen05 kernel; the BF16 output
+    # is the FP32 one rounded to nearest even
+    rng = np.random.default_rng(cin * 7 + cout)
+    x = rng.normal(size=(n, cin, h, w)).astype(np.float32)
+    wt = (rng.normal(size=(cout, cin, 3, 3)) * 0.1).astype(np.float32)
+    b = rng.normal(size=cout).astype(np.float32)
+    out = torch.full((n, cout, h, w), float("nan"), dtype=torch.float32, device="cuda")
+    outb = torch.empty((n, cout, h, w), dtype=torch.bfloat16, device="cuda")
+    m.mpv_cnn_conv3x3(_bf(x), _bf(wt), torch.from_numpy(b).cuda(), cout, relu, out_bf16=outb,
+                      out_f32=out)
+    xq, wq = cnn_ref.bf16(x), cnn_ref.bf16(wt)
+    want = cnn_ref.conv3x3(xq, wq, b)
+    if relu:
+        want = np.maximum(want, 0)
+    scale = cnn_ref.conv3x3(np.abs(xq), np.abs(wq)) + np.abs(b)[None, :, None, None]
+    got = out.cpu().numpy()
+    assert np.all(np.abs(got - want) <= 1e-5 * scale + 1e-6)
+    assert torch.equal(outb, out.to(torch.bfloat16))
+
+
 def test_conv_fp32_input_one_channel_out(m):
     rng = np.random.default_rng(1)
     x = rng.normal(size=(1, 32, 20, 17)).astype(np.float32)
