@@ -460,6 +460,7 @@ def run_mine(args):
             "gpu_launches": int(round(launches_per_frame * args.steps)),
             "clocks": clk,
             "wall_s_timed_region": round(wall, 4),
+            "device": device_info(dev),
         }
     mpv.mpv_destroy(ctx)
     if world > 1:
@@ -471,6 +472,8 @@ def run_mine(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not lw:
         # (the oracle has no network: the learned variants report no CPU baseline)
         out["cpu_baseline"] = cpu_baseline_full(L, R, args.variant)
+        if not args.no_extras:
+            out["cpu_baseline"]["per_config"] = oracle_per_config()
     if out is not None:
         print(json.dumps(out), flush=True)
 
@@ -495,6 +498,60 @@ def _oracle_pair(job):
     t = time.perf_counter()
     ref.match(L, R, p)
     return time.perf_counter() - t
+
+
+def device_info(dev):
+    """Name, SM count and L2 size (cudaDevAttrL2CacheSize) of the timed GPU."""
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    return {"name": p.name, "sms": p.multi_processor_count,
+            "l2_bytes": getattr(p, "L2_cache_size", None),
+            "hbm_bytes": p.total_memory}
+
+
+def _oracle_job(job):
+    """One generated pair of another configuration through the oracle (worker process):
+    (kind, W, H, D, seed, scales, paths) -> seconds."""
+    kind, w, h, d, seed, scales, paths = job
+    from oracle import ref
+    from paper_2001_09678_gb300 import synth
+    if kind == "bands":
+        L, R, _ = synth.bands_pair(w, h, seed=seed)
+    else:
+        L, R, _ = synth.slanted_pair(w, h, seed=seed, d_max=min(120.0, d - 8.0))
+    p = ref.params(window=0, block=(0, 0, 0, 0),
+                   **dict(PARAMS, max_disparity=d, num_scales=scales, num_paths=paths))
+    ref.lib()
+    t = time.perf_counter()
+    ref.match(L, R, p)
+    return time.perf_counter() - t
+
+
+def oracle_per_config():
+    """Single-core oracle seconds for configuration 1 and for four representative pairs of
+    the 64-pair batch (one 640x480 D64, two 1280x720 D128, one 1920x1080 D192), each in
+    its own process, run side by side."""
+    import multiprocessing as mp
+    from paper_2001_09678_gb300 import synth
+    specs = synth.mixed_batch_specs()
+    pick = []
+    for (w, h, d) in ((640, 480, 64), (1280, 720, 128), (1280, 720, 128), (1920, 1080, 192)):
+        seed = next(s for s, sw, sh, sd in specs if (sw, sh, sd) == (w, h, d) and
+                    all(s != q[4] for q in pick))
+        pick.append(("slanted", w, h, d, seed, 3, 8))
+    jobs = [("bands", 320, 240, 32, 0, 1, 4)] + pick
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        secs = pool.map(_oracle_job, jobs, chunksize=1)
+    return {"config1": {"seconds": round(secs[0], 3), "cores": 1,
+                        "value": round(320 * 240 * 32 / secs[0] / 1e6, 3), "unit": UNIT,
+                        "sample": "the 320x240 bands pair (seed 0), D=32, 1 scale, 4 paths, LR"},
+            "config3_representative": [
+                {"width": j[1], "height": j[2], "max_disparity": j[3], "seed": j[4],
+                 "seconds": round(s, 2), "cores": 1,
+                 "value": round(j[1] * j[2] * j[3] / s / 1e6, 3), "unit": UNIT}
+                for j, s in zip(pick, secs[1:])],
+            "note": "one process per pair, side by side on the host cores; every pair of the "
+                    "64-pair batch is verified against the oracle in the GPU tests"}
 
 
 def cpu_baseline_full(L, R, variant="plain"):
@@ -686,6 +743,34 @@ def bench_extras(dev, L, R, plain_ms):
             "fallbacks": falls, "frames": frames,
             "workload": f"the bench pair, learned proposal (committed network), finest window "
                         f"{lw}, default fallback (pyramid above 15 % edge hits), L2 flushed"}
+    # configuration 1: 320x240, D=32, one scale, 4 paths, LR; its 4.9 MB volume stays in
+    # L2, so only its latency is reported (no flush between frames)
+    from paper_2001_09678_gb300 import synth
+    L1, R1, _ = synth.bands_pair(320, 240, seed=0)
+    l1, r1 = torch.from_numpy(L1).to(dev), torch.from_numpy(R1).to(dev)
+    d1 = torch.empty((240, 320), dtype=torch.int16, device=dev)
+    ctx = mpv.mpv_create(dev.index)
+    mpv.mpv_set_params(ctx, mpv.mpv_default_params(**dict(PARAMS, max_disparity=32,
+                                                          num_scales=1, num_paths=4)))
+    for _ in range(20):
+        mpv.mpv_match(ctx, l1, r1, d1, stream)
+    mpv.mpv_sync(ctx)
+    n = 500
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(n)]
+    for a, b in ev:
+        a.record(stream)
+        mpv.mpv_match(ctx, l1, r1, d1, stream)
+        b.record(stream)
+    mpv.mpv_sync(ctx)
+    mpv.mpv_destroy(ctx)
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    out["config1"] = {
+        "ms_per_step": round(sum(ms) / n, 4), "p50_ms": round(ms[n // 2], 4),
+        "p99_ms": round(ms[int(0.99 * n)], 4), "samples": n,
+        "value": round(320 * 240 * 32 / (sum(ms) / n * 1e-3) / 1e6, 1), "unit": UNIT,
+        "workload": "320x240 bands pair (seed 0), D=32, 1 scale, 4 paths, p1=10, T=30, LR; "
+                    "cost volume L2-resident: latency only, no roofline"}
     out["batch64"] = measure_batch64(5, 2, serial=False)
     out["batch64"]["workload"] = ("16x640x480 D64 + 32x1280x720 D128 + 16x1920x1080 D192, "
                                   "3 scales, 8 paths, LR, one CUDA graph per batch")
