@@ -658,7 +658,7 @@ def measure_batch64(steps, warmup, serial=True):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
-    persistent, lanes, queues, cblocks, p_ms, s_ms = mpv.mpv_batch_info(ctx)
+    persistent, lanes, queues, cblocks, p_ms, s_ms, occ = mpv.mpv_batch_info(ctx)
     mpv.mpv_destroy(ctx)
     out = {"value": round(units / ms / 1e3, 1), "unit": UNIT, "ms_per_batch": round(ms, 3),
            "pairs_per_s": round(64e3 / ms, 1), "steps": steps, "warmup": warmup,
@@ -667,7 +667,8 @@ def measure_batch64(steps, warmup, serial=True):
            # stream graph on this batch, and the path it kept
            "path": "persistent kernel" if persistent else "stream graph",
            "tuner_ms": {"persistent": round(p_ms, 3), "streams": round(s_ms, 3)},
-           "persistent_shapes": {"lanes": lanes, "queues": queues, "cost_blocks": cblocks}}
+           "persistent_shapes": {"lanes": lanes, "queues": queues, "cost_blocks": cblocks,
+                                 "blocks_per_sm": occ}}
     if serial:
         seq_ms = _serial_ms(mpv, pairs, stream, max(1, steps // 4), warmup)
         out.update({"serial_ms_per_64_pairs": round(seq_ms, 3),

@@ -243,13 +243,15 @@ mpv_status mpv_sync(mpv_ctx *ctx);
  * claimable item is the one device-side wait, bounded in clock cycles (about 2 s): when
  * it runs out the batch stops and mpv_sync returns MPV_ERR_TIMEOUT.  Once per set of
  * pair shapes the autotuner times the persistent kernel with each candidate shape
- * (lanes per scan path, work queues, cost blocks per item) and the stream graph on the
+ * (lanes per scan path, work queues, cost blocks per item), then with 3 and 4 resident
+ * blocks per SM (its register budget) for the best shape, and the stream graph, on the
  * batch itself, and keeps the fastest; all give the same bit-exact maps.
  * mpv_batch_info reports the path of the context's last batch (persistent 1 or 0), the
- * persistent shapes and the tuner's times in milliseconds per batch (0 when not tuned). */
+ * persistent shapes, the tuner's times in milliseconds per batch (0 when not tuned) and
+ * the persistent kernel's resident blocks per SM.  Any output pointer may be NULL.     */
 mpv_status mpv_batch_info(const mpv_ctx *ctx, int32_t *persistent, int32_t *lanes,
                           int32_t *queues, int32_t *cost_blocks, float *persistent_ms,
-                          float *streams_ms);
+                          float *streams_ms, int32_t *occupancy);
 
 /* Which batch path mpv_match_batch takes: MPV_BATCH_AUTO (default: the autotuner's
  * choice), MPV_BATCH_PERSISTENT (the persistent kernel wherever it applies) or

@@ -236,7 +236,12 @@ __device__ int claim(const BItem *items, const BQueue *queues, int nq, const int
     }
 }
 
-__global__ void __launch_bounds__(kBT, 2)
+// MINB: resident blocks per SM the kernel is compiled for.  One kernel holds every item
+// kind, so the register budget of its largest item (a stencil pass) caps them all: 2
+// gives the passes their registers, 3 and 4 trade spills in the passes for more warps
+// in every other item; the batch autotuner times each.
+template <int MINB>
+__global__ void __launch_bounds__(kBT, MINB)
 batch_kernel(const BPair *pairs, const BItem *items, const BQueue *queues, int nq,
              const int *totals, BState *st, long long wait_cycles)
 {
@@ -526,34 +531,45 @@ mpv_status upload_batch(const BatchPlan &plan, void *dev, BatchDevice &out)
     return MPV_OK;
 }
 
-mpv_status launch_batch(const BatchDevice &bd, long long wait_cycles, int *status_host,
-                        cudaStream_t s)
+template <int MINB>
+mpv_status launch_batch_t(const BatchDevice &bd, long long wait_cycles, int *status_host,
+                          cudaStream_t s)
 {
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (bd.smem > 48 * 1024 &&
-        cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(batch_kernel<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bd.smem) != cudaSuccess) {
         cudaGetLastError();
         return MPV_ERR_UNSUPPORTED;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBT, bd.smem) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<MINB>, kBT,
+                                                      bd.smem) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         return MPV_ERR_UNSUPPORTED;
     }
     const int grid = std::max(1, std::min(nsm * per_sm, bd.nitems));
     cudaMemsetAsync(bd.state, 0, bd.state_bytes, s);
-    batch_kernel<<<grid, kBT, bd.smem, s>>>((const BPair *)bd.pairs, (const BItem *)bd.items,
-                                            (const BQueue *)bd.queues, bd.nqueues,
-                                            (const int *)bd.totals, (BState *)bd.state,
-                                            wait_cycles);
+    batch_kernel<MINB><<<grid, kBT, bd.smem, s>>>(
+        (const BPair *)bd.pairs, (const BItem *)bd.items, (const BQueue *)bd.queues, bd.nqueues,
+        (const int *)bd.totals, (BState *)bd.state, wait_cycles);
     if (status_host)
         cudaMemcpyAsync(status_host, bd.state, sizeof(int), cudaMemcpyDeviceToHost, s);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPV_OK : MPV_ERR_CUDA;
+}
+
+mpv_status launch_batch(const BatchDevice &bd, long long wait_cycles, int *status_host,
+                        cudaStream_t s)
+{
+    switch (bd.occupancy) {
+    case 2: return launch_batch_t<2>(bd, wait_cycles, status_host, s);
+    case 3: return launch_batch_t<3>(bd, wait_cycles, status_host, s);
+    case 4: return launch_batch_t<4>(bd, wait_cycles, status_host, s);
+    default: return MPV_ERR_INVALID_ARG;
+    }
 }
 
 }  // namespace mpv

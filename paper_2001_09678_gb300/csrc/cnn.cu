@@ -436,7 +436,9 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(
         constexpr int kBatch = 8;
         if (NHWC) {
             const __nv_bfloat16 *src = in + (int64_t)n * cstr * plane;
-            const int per = cstr / 8, npieces = kTcPix * per;
+            // 16-byte pieces per pixel, never more than the planes the operand holds
+            // (channels Cin .. cstr - 1 are zero, so those beyond the planes are not needed)
+            const int per = min(cstr / 8, ncg), npieces = kTcPix * per;
             for (int i0 = tid; i0 < npieces; i0 += 128 * kBatch) {
                 uint4 v[kBatch];
 #pragma unroll

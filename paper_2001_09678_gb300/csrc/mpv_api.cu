@@ -364,7 +364,9 @@ mpv_status run_batch_persistent(mpv_ctx *ctx, const PairJob *jobs, int n, cudaSt
             cudaGetLastError();
             return cuda_status(e);
         }
-        return upload_batch(plan, *dev, bd);
+        r = upload_batch(plan, *dev, bd);
+        bd.occupancy = t.occupancy;
+        return r;
     };
 
     // the launch shapes: tuned once per set of pair shapes
@@ -379,6 +381,29 @@ mpv_status run_batch_persistent(mpv_ctx *ctx, const PairJob *jobs, int n, cudaSt
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
+        // times one candidate; false when the batch failed (status in r)
+        auto trial = [&](const BatchTune &t, mpv_status &r) {
+            void *dev = nullptr;
+            BatchDevice bd;
+            r = build(t, &dev, bd);
+            float ms = 1e30f;
+            if (r == MPV_OK) {
+                r = launch_batch(bd, ctx->wait_cycles, ctx->bstatus_host, s);   // warm
+                cudaEventRecord(e0, s);
+                if (r == MPV_OK) r = launch_batch(bd, ctx->wait_cycles, ctx->bstatus_host, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                if (r == MPV_OK && *ctx->bstatus_host == MPV_OK) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (dev) cudaFree(dev);
+            if (r == MPV_OK && ms < best) {
+                best = ms;
+                tune = t;
+            }
+            return r == MPV_OK;
+        };
+        mpv_status tr = MPV_OK;
+        bool ok = true;
         for (int lanes : {8, 4})
             for (int queues : {16, 32})
                 for (int cb : {2, 8}) {
@@ -386,30 +411,19 @@ mpv_status run_batch_persistent(mpv_ctx *ctx, const PairJob *jobs, int n, cudaSt
                     t.lanes = lanes;
                     t.queues = queues;
                     t.cost_blocks = cb;
-                    void *dev = nullptr;
-                    BatchDevice bd;
-                    mpv_status r = build(t, &dev, bd);
-                    float ms = 1e30f;
-                    if (r == MPV_OK) {
-                        r = launch_batch(bd, ctx->wait_cycles, ctx->bstatus_host, s);   // warm
-                        cudaEventRecord(e0, s);
-                        if (r == MPV_OK) r = launch_batch(bd, ctx->wait_cycles, ctx->bstatus_host, s);
-                        cudaEventRecord(e1, s);
-                        cudaEventSynchronize(e1);
-                        if (r == MPV_OK && *ctx->bstatus_host == MPV_OK)
-                            cudaEventElapsedTime(&ms, e0, e1);
-                    }
-                    if (dev) cudaFree(dev);
-                    if (r != MPV_OK) {
-                        cudaEventDestroy(e0);
-                        cudaEventDestroy(e1);
-                        return r;
-                    }
-                    if (ms < best) {
-                        best = ms;
-                        tune = t;
-                    }
+                    if (ok) ok = trial(t, tr);
                 }
+        // then the register budget, with the best shapes
+        for (int occ : {3, 4}) {
+            BatchTune t = tune;
+            t.occupancy = occ;
+            if (ok) ok = trial(t, tr);
+        }
+        if (!ok) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return tr;
+        }
         // the same batch as a graph of per-pair launch sequences over worker streams
         float streams_ms = 1e30f;
         {
@@ -1142,13 +1156,14 @@ mpv_status mpv_debug_batch_stall(mpv_ctx *ctx, int64_t wait_cycles)
 
 mpv_status mpv_batch_info(const mpv_ctx *ctx, int32_t *persistent, int32_t *lanes,
                           int32_t *queues, int32_t *cost_blocks, float *persistent_ms,
-                          float *streams_ms)
+                          float *streams_ms, int32_t *occupancy)
 {
     if (!ctx) return MPV_ERR_INVALID_ARG;
     const BatchTune &t = ctx->last_batch;
     if (persistent) *persistent = t.persistent ? 1 : 0;
     if (lanes) *lanes = t.lanes;
     if (queues) *queues = t.queues;
+    if (occupancy) *occupancy = t.occupancy;
     if (cost_blocks) *cost_blocks = t.cost_blocks;
     if (persistent_ms) *persistent_ms = t.ms;
     if (streams_ms) *streams_ms = t.streams_ms;

@@ -312,6 +312,8 @@ struct BatchTune {
     int lanes = 8;         // lanes per scan path of the 32-label passes (8 or 4)
     int queues = 16;       // work queues (groups of pairs, like streams)
     int cost_blocks = 4;   // cost-kernel blocks per work item
+    int occupancy = 2;     // resident blocks per SM the persistent kernel is built for
+                           // (2, 3 or 4: fewer registers a thread, more warps)
     bool stall = false;    // test hook: one stage never completes (bounded-wait test)
     int *err = nullptr;    // bounds-checked builds: the device error word
     // the tuner's verdict: the persistent kernel was faster than the stream graph, with
@@ -326,6 +328,7 @@ struct BatchDevice {
     void *state = nullptr;   // cleared before every launch: status, abort, heads, counters
     size_t state_bytes = 0, smem = 0;
     int nqueues = 0, nitems = 0;
+    int occupancy = 2;   // BatchTune::occupancy of the launch
 };
 
 class BatchPlan {

@@ -163,7 +163,7 @@ def load(path: str = LIB_PATH):
     L.mpv_proposal_features.argtypes = [ctx, vp, vp, i32, i32, i32, i32, vp, vp]
     L.mpv_proposal_stats.argtypes = [ctx, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     L.mpv_proposal_fallbacks.argtypes = [ctx, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
-    L.mpv_batch_info.argtypes = [ctx] + [C.POINTER(i32)] * 4 + [C.POINTER(C.c_float)] * 2
+    L.mpv_batch_info.argtypes = [ctx] + [C.POINTER(i32)] * 4 + [C.POINTER(C.c_float)] * 2 + [C.POINTER(i32)]
     L.mpv_debug_batch_stall.argtypes = [ctx, C.c_int64]
     L.mpv_set_batch_mode.argtypes = [ctx, i32]
     L.mpv_destroy.argtypes = [ctx]
@@ -481,9 +481,9 @@ def mpv_proposal_stats(ctx):
 
 
 def mpv_batch_info(ctx):
-    """(persistent, lanes, queues, cost_blocks, persistent_ms, streams_ms) of the
-    context's last batch."""
-    v = [C.c_int32() for _ in range(4)] + [C.c_float() for _ in range(2)]
+    """(persistent, lanes, queues, cost_blocks, persistent_ms, streams_ms, occupancy) of
+    the context's last batch."""
+    v = [C.c_int32() for _ in range(4)] + [C.c_float() for _ in range(2)] + [C.c_int32()]
     _check(load().mpv_batch_info(ctx, *[C.byref(x) for x in v]), "mpv_batch_info")
     return tuple(x.value for x in v)
 

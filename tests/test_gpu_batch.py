@@ -169,8 +169,8 @@ def test_persistent_batch_and_its_bounded_wait(mpv):
         # accumulates into, whatever the memory held before
         _run_batch(mpv, ctx, [(R, L, D) for L, R, D in pairs], repeats=1)
         runs = _run_batch(mpv, ctx, pairs, repeats=2)
-        persistent, lanes, queues, cb, pms, sms = mpv.mpv_batch_info(ctx)
-        assert persistent == 1 and lanes in (4, 8) and queues in (16, 32) and cb in (2, 8)
+        persistent, lanes, queues, cb, pms, sms, occ = mpv.mpv_batch_info(ctx)
+        assert persistent == 1 and lanes in (4, 8) and queues in (16, 32) and cb in (2, 8) and occ in (2, 3, 4)
         assert pms > 0 and sms > 0                     # the tuner timed both paths
         for run in runs:
             for got, w in zip(run, want):
