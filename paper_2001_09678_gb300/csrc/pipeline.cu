@@ -1,5 +1,6 @@
 // pipeline.cu -- validation, pyramid geometry, workspace layout and the launch sequence
 // of one stereo pair, shared by every entry point of the C ABI.
+#include <nvtx3/nvToolsExt.h>
 #include "mpv_internal.cuh"
 
 namespace mpv {
@@ -25,17 +26,24 @@ size_t take(size_t &off, size_t bytes)
     return at;
 }
 
+// Names of the stages as NVTX ranges (host side: the span in which a stage's launches
+// are enqueued or captured; no-ops unless a tool such as ncu --nvtx is attached).
+const char *const kStageRange[] = {"mpv:pyramid", "mpv:seed", "mpv:cost", "mpv:aggregate",
+                                   "mpv:wta", "mpv:lr"};
+
 struct HookScope {
     const StageHook *h;
     int stage;
     cudaStream_t s;
     HookScope(const StageHook *h_, int stage_, int nk, cudaStream_t s_) : h(h_), stage(stage_), s(s_)
     {
+        nvtxRangePushA(stage >= 0 && stage < 6 ? kStageRange[stage] : "mpv:stage");
         if (h && h->begin) h->begin(h->user, stage, nk, s);
     }
     ~HookScope()
     {
         if (h && h->end) h->end(h->user, stage, s);
+        nvtxRangePop();
     }
 };
 
