@@ -87,7 +87,33 @@ __device__ __forceinline__ void seed_body(const SeedArgs &a, int x, int y, int v
     const uint16_t *dp = a.dprev[view];
     if (!MPV_IN(a.err, (x >> 1) < a.Wp && (y >> 1) < a.Hp, 11)) return;
     int c;
-    if (a.block >= 2) {
+    if (a.block == 2) {
+        // the same rule on the block's (up to) four values, each loaded once
+        const int qx0 = (x >> 1) & ~1, qy0 = (y >> 1) & ~1;
+        const bool hx = qx0 + 1 < a.Wp, hy = qy0 + 1 < a.Hp;
+        const uint16_t *r0 = dp + (int64_t)qy0 * a.Wp + qx0;
+        int v[4], ok[4];
+        v[0] = r0[0];
+        ok[0] = 1;
+        v[1] = hx ? r0[1] : 0;
+        ok[1] = hx;
+        v[2] = hy ? r0[a.Wp] : 0;
+        ok[2] = hy;
+        v[3] = (hx && hy) ? r0[a.Wp + 1] : 0;
+        ok[3] = hx && hy;
+        int best = 0x7FFFFFFF, best_n = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            int m = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) m += ok[q] && v[q] == v[p];
+            if (ok[p] && (m > best_n || (m == best_n && v[p] < best))) {
+                best = v[p];
+                best_n = m;
+            }
+        }
+        c = 2 * best;
+    } else if (a.block >= 2) {
         // mode of the doubled coarse disparities of the block, ties to the smaller value
         const int b = a.block;
         const int qx0 = ((x >> 1) / b) * b, qy0 = ((y >> 1) / b) * b;
