@@ -119,8 +119,13 @@ __device__ __forceinline__ void cost_body(const LevelArgs &a, int uspan_max, int
     const ViewLevel &V = a.v[view];
     const int W = a.W, H = a.H, Dw = a.Dw, Dws = a.Dws;
     const int y = by;
-    const int x0 = bx * kSegPix;
-    const int npx = min(kSegPix, W - x0);
+    // the row's ceil(W / kSegPix) segments of equal width, a multiple of 32 pixels (whole
+    // pixels for every warp and sub-stream): the widest block sets a launch's time
+    const int nseg = (W + kSegPix - 1) / kSegPix;
+    const int seg = min(kSegPix, ((W + nseg - 1) / nseg + 31) & ~31);
+    const int x0 = bx * seg;
+    const int npx = min(seg, W - x0);
+    if (npx <= 0) return;   // (whole block; only for rows far wider than 8192 pixels)
     const int c1 = a.c1, c2 = a.c2;
 
     __shared__ int lo_s[kSegPix];
@@ -201,7 +206,7 @@ __device__ __forceinline__ void cost_body(const LevelArgs &a, int uspan_max, int
     const int LP = Dws < 32 ? Dws : 32;     // lanes per pixel stream
     const int nsub = 32 / LP;
     const int sub = lane / LP, kl = lane - sub * LP;
-    const int per_warp = kSegPix / kCostWarps;
+    const int per_warp = seg / kCostWarps;
     const int sub_len = per_warp / nsub;
     const int xs = warp * per_warp + sub * sub_len;      // segment-relative
     const int xe = min(xs + sub_len, npx);
