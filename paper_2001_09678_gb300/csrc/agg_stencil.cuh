@@ -368,9 +368,11 @@ __device__ __forceinline__ void agg_stencil_body(const LevelArgs &a, const Merge
                 __syncwarp();
                 const uint4 *g4 = (const uint4 *)(rw + grp * kG);
                 const uint4 q0 = g4[0];
-                const uint32_t r = __vminu2(__vminu2(q0.x, q0.y), __vminu2(q0.z, q0.w));
                 const uint4 q1 = g4[1];
-                m2 = __vminu2(r, __vminu2(__vminu2(q1.x, q1.y), __vminu2(q1.z, q1.w)));
+                // 3-input packed minima: two dependent levels instead of three
+                const uint32_t r0 = __vimin3_u16x2(q0.x, q0.y, q0.z);
+                const uint32_t r1 = __vimin3_u16x2(q0.w, q1.x, q1.y);
+                m2 = __vimin3_u16x2(r0, r1, __vminu2(q1.z, q1.w));
             }
             if (OUTN && t > 0 && t - 1 < n)   // the previous pixel, normalised by its minimum
                 store_normalised<KW>(outv + (int64_t)(pix - dpix) * DWP + gl * K, A, m2, keep,
@@ -469,9 +471,9 @@ __device__ __forceinline__ void agg_stencil_body(const LevelArgs &a, const Merge
 #pragma unroll
                 for (int i = 0; i < KW; ++i) {
                     const int e = HW + i;
-                    // words below e hold smaller labels: jumps up into (u, u+1)
-                    uint32_t m = __vminu2(E[e], cap);
-                    m = __viaddmin_u16x2(SH[e - 1], U1, m);
+                    // words below e hold smaller labels: jumps up into (u, u+1); the cap
+                    // (which waits for the path minimum) enters last
+                    uint32_t m = __viaddmin_u16x2(SH[e - 1], U1, E[e]);
                     m = __viaddmin_u16x2(SH[e], E1, m);
                     m = __viaddmin_u16x2(E[e - 1], U2, m);
                     m = __viaddmin_u16x2(E[e + 1], E2, m);
@@ -482,6 +484,7 @@ __device__ __forceinline__ void agg_stencil_body(const LevelArgs &a, const Merge
                         m = __viaddmin_u16x2(E[e + 2], E4, m);
                     }
                     if (asym) m = __viaddmin_u16x2(SA[i], Tx2, m);
+                    m = __vminu2(m, cap);
                     uint32_t L = c[i] + m - m2;      // per half: no carry, no borrow
                     if (padded) {
                         L &= keep[i];
