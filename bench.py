@@ -32,6 +32,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Load every kernel when the process starts instead of at its first launch: a lazy load
+# in the middle of the served streams held the host for tens of milliseconds (set before
+# CUDA initialises; an explicit setting in the environment wins).
+os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
 
 W, H, D = 1280, 720, 128
 PARAMS = dict(max_disparity=D, num_scales=3, num_paths=8, p1=10, trunc=30, ssim_window=5,

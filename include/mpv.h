@@ -299,7 +299,10 @@ mpv_status mpv_level_info(const mpv_ctx *ctx, int32_t width, int32_t height, int
  * admitted cameras fits hbm_budget (0 = no limit); idle cameras are evicted least
  * recently used first to make room.  Admitted frames of different cameras run
  * concurrently on the GPU.  The server is used from one host thread; nothing blocks on
- * the GPU.  Results equal mpv_match of the same pair alone.                           */
+ * the GPU.  Results equal mpv_match of the same pair alone.  A serving process should
+ * load its kernels at start-up (CUDA_MODULE_LOADING=EAGER in its environment before CUDA
+ * initialises): with lazy loading, a kernel's first launch while other frames are in
+ * flight (a proposal's first fallback, say) held the host for tens of milliseconds.      */
 typedef struct mpv_server mpv_server;
 
 typedef struct {

@@ -154,6 +154,9 @@ def run(cams, pools, seconds=5.0, hz=30.0, budget=0, max_inflight=8, params=None
 
 
 def main():
+    # every kernel loaded at start-up: a lazy load while frames are in flight holds the host
+    # (set before CUDA initialises; an explicit setting in the environment wins)
+    os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
     ap = argparse.ArgumentParser()
     ap.add_argument("--seconds", type=float, default=10.0)
     ap.add_argument("--hz", type=float, default=30.0)
