@@ -452,6 +452,12 @@ def run_mine(args):
                 "traffic_over_alg": (round(traffic_step / alg[dom], 2) if traffic_step else None),
                 "alg_bytes_per_node": ALG_NOTE[dom],
                 "frac_at_survey_bytes": round(achieved4 / peak, 4),
+                # the whole path: every stage's algorithmic bytes of one frame over the
+                # frame time (the survey's whole-path figure reads a uint16 cost: the second)
+                "whole_path": {"alg_bytes_per_step": int(sum(alg.values())),
+                               "frac": round(sum(alg.values()) / (ms_per_step * 1e-3) / 1e9 / peak, 4),
+                               "frac_at_survey_bytes": round(sum(alg4.values()) / (ms_per_step * 1e-3)
+                                                             / 1e9 / peak, 4)},
                 # the integer path's second bound: ALU-pipe and issue-slot activity of the
                 # same kernel (ncu, device-time weighted over the frame's launches)
                 "int_pipe": (dict(alu_pipe_active=counters["alu_pipe_active"],
