@@ -38,10 +38,12 @@ __global__ void __launch_bounds__(2 * kPyrCols) pyramid2_kernel(PyrJobs4 jobs, i
     pyramid2_body(jobs.j[blockIdx.z], W, H, blockIdx.x, blockIdx.y, threadIdx.x, t1);
 }
 
-__global__ void seed_kernel(SeedArgs a)
+// One block per row (blockIdx.x) and view (blockIdx.y); the threads stride over the row.
+__global__ void __launch_bounds__(256) seed_kernel(SeedArgs a)
 {
     if (a.gate && *a.gate == 0) return;
-    seed_body(a, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
+#pragma unroll 4
+    for (int x = threadIdx.x; x < a.W; x += blockDim.x) seed_body(a, x, blockIdx.x, blockIdx.y);
 }
 
 template <int LPP>
@@ -149,8 +151,7 @@ void launch_pyramid2(const PyrJob *jobs, int njobs, int W, int H, cudaStream_t s
 
 void launch_seed(const SeedArgs &a, cudaStream_t s)
 {
-    dim3 grid((a.W + 127) / 128, a.H, a.nviews);
-    seed_kernel<<<grid, 128, 0, s>>>(a);
+    seed_kernel<<<dim3(a.H, a.nviews, 1), 256, 0, s>>>(a);
 }
 
 void launch_wta(const LevelArgs &a, cudaStream_t s)
