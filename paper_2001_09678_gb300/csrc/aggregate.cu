@@ -58,6 +58,83 @@ void launch_stencil(const LevelArgs &a, cudaStream_t s, const MergeArgs &mg = Me
     agg_stencil<G, KW, RM, WIN, BLK, LAYER, SWP, XM><<<grid, kStencilWarps * 32, 0, s>>>(a, mg);
 }
 
+// The summed pass of the 8-lane shape with the row (horizontal) paths first: one 1-D grid
+// whose first nviews x 2 x nhb blocks run the two row directions of both views, the rest
+// the other directions (2 .. npaths - 1, nbx blocks each).  Blocks start in index order, so
+// the longest chains (W steps) start first.  The rows run agg_row_body on levels without
+// windows and agg_stencil_body with them (measured at 1280x720, D = 128: 320x180 without
+// windows 36.9 -> 34.8 us with the row body; 640x360 with windows 102.4 us with the
+// stencil body, 112.7 us with the row body, whose separate code also has to be fetched).
+template <bool WIN>
+__global__ void __launch_bounds__(kStencilWarps * 32) agg_rows_first(LevelArgs a, MergeArgs mg,
+                                                                   int nhb, int nbx)
+{
+    if (a.gate && *a.gate == 0) return;
+    using SM = StencilSmem<8, 2, 2, WIN, false, false, kStencilWarps>;
+    __shared__ __align__(16) unsigned char smem[SM::bytes];
+    int b = blockIdx.x;
+    const int nrow = a.nviews * 2 * nhb;
+    int bx, by, view;
+    if (b < nrow) {
+        view = b / (2 * nhb);
+        const int r = b - view * 2 * nhb;
+        by = r / nhb;
+        bx = r - by * nhb;
+        if constexpr (!WIN) {
+            if (by == 0) agg_row_body<1, WIN, kStencilWarps>(a, bx, view, threadIdx.x, smem);
+            else agg_row_body<-1, WIN, kStencilWarps>(a, bx, view, threadIdx.x, smem);
+            return;
+        }
+    } else {
+        b -= nrow;
+        const int per_view = (a.npaths - 2) * nbx;
+        view = b / per_view;
+        const int r = b - view * per_view;
+        by = 2 + r / nbx;
+        bx = r - (by - 2) * nbx;
+    }
+    agg_stencil_body<8, 2, 2, WIN, false, false, false, true, kStencilWarps>(
+        a, mg, bx, by, view, threadIdx.x, smem);
+}
+
+// Whether the rows-first launch applies and pays: the level's blocks fit in about one and
+// a half waves of the GPU, so the W-step row chains, not the throughput of the other
+// directions, set the launch's time (measured at 1280x720, D = 128: 320x180 36.9 -> 34.8
+// us, 640x360 108.5 -> 102.4 us; at 1280x720 itself, 2.2 waves, the library order is as
+// fast or faster, 336 against 336-340 us).
+template <bool WIN>
+bool rows_first(const LevelArgs &a, int &nhb, int &nbx)
+{
+    if (a.npaths != 4 && a.npaths != 8) return false;
+    constexpr int per_block = kStencilWarps * 4;   // 4 paths of 8 lanes per warp
+    nhb = (a.H + per_block - 1) / per_block;
+    nbx = (a.W + a.H - 1 + per_block - 1) / per_block;
+    const int64_t blocks = (int64_t)a.nviews * (2 * nhb + (int64_t)(a.npaths - 2) * nbx);
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, agg_rows_first<WIN>,
+                                                      kStencilWarps * 32, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return blocks * 2 <= (int64_t)3 * nsm * per_sm && blocks < 0x7FFFFFFF;
+}
+
+template <bool WIN>
+bool launch_rows_first(const LevelArgs &a, cudaStream_t s)
+{
+    int nhb = 0, nbx = 0;
+    if (!rows_first<WIN>(a, nhb, nbx)) return false;
+    MergeArgs m{};
+    m.dir0 = 0;
+    m.ndirs = a.npaths;
+    m.double_up_dir = -1;
+    const int blocks = a.nviews * (2 * nhb + (a.npaths - 2) * nbx);
+    agg_rows_first<WIN><<<blocks, kStencilWarps * 32, 0, s>>>(a, m, nhb, nbx);
+    return true;
+}
+
 // Packed labels mark absent ones with the sentinel kInf16, which must exceed every cap
 // min_v A(v) + Tu that a step forms.  Without windows the predecessor's best label carries
 // over, so its minimum is at most a cost byte and the cap at most 255 + T.  With windows
@@ -78,6 +155,8 @@ void launch_stencil_kw(const LevelArgs &a, cudaStream_t s)
     // padding labels, slower with one word per lane or with padding
     if constexpr (G == 8 && KW == 2) {
         if (a.Dw == a.Dws && a.radius <= 2) {
+            if (!blk && (win ? launch_rows_first<true>(a, s) : launch_rows_first<false>(a, s)))
+                return;
             if (win) launch_stencil<G, KW, 2, true, false, false, false, true>(a, s);
             else if (blk) launch_stencil<G, KW, 2, false, true, false, false, true>(a, s);
             else launch_stencil<G, KW, 2, false, false, false, false, true>(a, s);
