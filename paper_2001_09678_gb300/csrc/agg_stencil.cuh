@@ -171,10 +171,10 @@ __device__ __forceinline__ void agg_stencil_body(const LevelArgs &a, const Merge
     constexpr int DWP = kG * K;              // labels per path (= the volume stride)
     constexpr int PAD = SM::PAD;             // absent labels around a path
     constexpr int BUF = SM::BUF;
-    // prefetch distance (steps), measured: 12 for the summed pass with two words per lane
-    // (8 lanes on 32 labels), 8 for the other shapes and for the layer and sweep modes
-    // (each slower at 12), 4 for the widest lanes
-    constexpr int PF = KW > 4 ? 4 : (KW == 2 && !LAYER && !SWP ? 12 : 8);
+    // prefetch distance (steps), measured: 10 for the summed pass with two words per lane
+    // (8 lanes on 32 labels; 8, 12 and 16 slower), 8 for the other shapes and for the layer
+    // and sweep modes (each slower at 12), 4 for the widest lanes
+    constexpr int PF = KW > 4 ? 4 : (KW == 2 && !LAYER && !SWP ? 10 : 8);
     constexpr int CW = KW >= 2 ? KW / 2 : 1; // 32-bit words of cost bytes per lane
     static_assert(kG == 4 || kG == 8, "paths of 4 or 8 lanes");
 
