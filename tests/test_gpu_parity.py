@@ -87,6 +87,12 @@ CASES = {
                            dict(max_disparity=64, num_scales=3, num_paths=8)),
     "odd_window_17": (lambda: synth.slanted_pair(256, 144, seed=17, d_max=100)[:2],
                       dict(max_disparity=128, num_scales=2, num_paths=8, window=17)),
+    # 32-label rows of 33 and 35 pixels (one straight-line chunk, then the guarded tail)
+    # and heights that leave part of the last warp's four rows outside the image
+    "narrow_33x50_d32": (lambda: synth.bands_pair(33, 50, seed=40, disparities=(2, 5, 9))[:2],
+                         dict(max_disparity=32, num_scales=1, num_paths=8)),
+    "narrow_70x45_win32": (lambda: synth.bands_pair(70, 45, seed=41, disparities=(4, 11, 20))[:2],
+                           dict(max_disparity=64, num_scales=2, num_paths=8, window=32)),
     # stencil radius ceil(T/p1) - 1 = 1, 3, 4 (the default p1=10, T=30 gives 2)
     "radius1": (lambda: synth.slanted_pair(192, 96, seed=18, d_max=40)[:2],
                 dict(max_disparity=48, num_scales=2, num_paths=8, p1=10, trunc=20)),
