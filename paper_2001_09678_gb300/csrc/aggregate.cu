@@ -21,7 +21,10 @@
 //    packed add-min arithmetic over halo words from the neighbouring lanes.  The path's
 //    minimum is exchanged through shared memory or by shuffles, a window shift between
 //    consecutive pixels (pyramid levels) re-indexes the predecessor through shared memory,
-//    and S is accumulated with 64-bit reductions of four packed labels.  Its layer mode
+//    and S is accumulated with 64-bit reductions of four packed labels.  While every path
+//    of a warp is active its steps run without per-lane checks.  On levels small enough
+//    to be resident at once, agg_rows_first starts the row paths (the W-step chains that
+//    bound such levels) ahead of the other directions in one grid.  Its layer mode
 //    runs one layer of the layered merge (Section 3.2), the left-to-right pass with doubled
 //    upward jumps included; its sweep mode runs gradient-weighted slopes (Eq. EU) as
 //    untruncated packed sweeps.
