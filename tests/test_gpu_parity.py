@@ -93,6 +93,10 @@ CASES = {
                          dict(max_disparity=32, num_scales=1, num_paths=8)),
     "narrow_70x45_win32": (lambda: synth.bands_pair(70, 45, seed=41, disparities=(4, 11, 20))[:2],
                            dict(max_disparity=64, num_scales=2, num_paths=8, window=32)),
+    # one view (no left-right check) and 4 paths: the row blocks of a single view
+    "narrow_40x29_d32_4p_nolr": (lambda: synth.bands_pair(40, 29, seed=42,
+                                                          disparities=(3, 8, 14))[:2],
+                                 dict(max_disparity=32, num_scales=1, num_paths=4, lr_check=0)),
     # stencil radius ceil(T/p1) - 1 = 1, 3, 4 (the default p1=10, T=30 gives 2)
     "radius1": (lambda: synth.slanted_pair(192, 96, seed=18, d_max=40)[:2],
                 dict(max_disparity=48, num_scales=2, num_paths=8, p1=10, trunc=20)),
